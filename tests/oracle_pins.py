@@ -1,0 +1,312 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each ``pin_*`` takes an ``oracle.Oracle`` and raises AssertionError when the
+oracle disagrees. ``tests/test_oracle_pins.py`` runs them on the oracle;
+``tests/test_oracle_mutants.py`` plants plausible mistakes in a copy of the
+oracle's C source and checks that at least one pin fails for each.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TWO32 = 1 << 32
+
+
+# --------------------------------------------------------------------------- #
+# Philox4x32-10: published known-answer vectors (Random123 / Salmon et al.)    #
+# --------------------------------------------------------------------------- #
+def load_kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(x, 16) for x in line.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def pin_philox_kat(o):
+    for ctr, key, want in load_kat():
+        got = [int(x) for x in o.philox(ctr, key)]
+        assert got == want, (ctr, key, [hex(g) for g in got], [hex(w) for w in want])
+
+
+# --------------------------------------------------------------------------- #
+# Payoffs, Eq. (1)-(2): hand-worked values and brute-force group membership    #
+# --------------------------------------------------------------------------- #
+def pattern_lattice(L: int, name: str) -> np.ndarray:
+    lat = np.zeros((L, L), dtype=np.uint8)
+    if name == "lone_c":
+        lat[0, 0] = 1
+    elif name == "pair_c":
+        lat[0, 0] = 1
+        lat[0, 1] = 1
+    elif name == "row_c":
+        lat[0, :] = 1
+    elif name == "all_c":
+        lat[:] = 1
+    elif name == "all_d":
+        pass
+    else:
+        raise ValueError(name)
+    return lat
+
+
+def load_hand_worked():
+    rows = []
+    with open(os.path.join(GOLDEN, "payoffs_hand_worked.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            L, r, pat, i, j, S, pay = line.split()
+            rows.append((int(L), float(r), pat, int(i), int(j), int(S), float(pay)))
+    return rows
+
+
+def pin_payoff_hand_worked(o):
+    for L, r, pat, i, j, S, pay in load_hand_worked():
+        lat = pattern_lattice(L, pat)
+        s = int(lat[i, j])
+        assert o.group_count_total(lat, i, j) == S, (L, pat, i, j)
+        assert abs(o.payoff_groups(lat, i, j, r) - pay) < 1e-12, (L, pat, i, j, "groups")
+        assert abs(o.payoff_total(s, S, r) - pay) < 1e-12, (L, pat, i, j, "total")
+
+
+def brute_force_payoffs(lat: np.ndarray, r: float):
+    """Payoffs by explicit group membership: build every group G_z (centre z plus
+    its four neighbours, as a list with multiplicity), then give each player the
+    Eq. (1)-(2) share of every group it is a member of."""
+    L = lat.shape[0]
+    groups = {}
+    for zi in range(L):
+        for zj in range(L):
+            groups[(zi, zj)] = [(zi, zj), ((zi + 1) % L, zj), ((zi - 1) % L, zj),
+                                (zi, (zj + 1) % L), (zi, (zj - 1) % L)]
+    pay = np.zeros((L, L))
+    tot = np.zeros((L, L), dtype=np.int64)
+    for z, members in groups.items():
+        nc = sum(int(lat[m]) for m in members)
+        for x in set(members):
+            s = int(lat[x])
+            share = r * nc / 5.0 - (1.0 if s else 0.0)
+            pay[x] += share
+            tot[x] += nc
+    return pay, tot
+
+
+def pin_payoff_brute_force(o):
+    rng = np.random.default_rng(1234)
+    for L in (3, 4, 5, 8):
+        for trial in range(3):
+            lat = (rng.random((L, L)) < 0.5).astype(np.uint8)
+            r = float(rng.uniform(1.5, 5.5))
+            pay, tot = brute_force_payoffs(lat, r)
+            for i in range(L):
+                for j in range(L):
+                    assert o.group_count_total(lat, i, j) == tot[i, j], (L, i, j)
+                    assert abs(o.payoff_groups(lat, i, j, r) - pay[i, j]) < 1e-9, (L, i, j)
+                    s = int(lat[i, j])
+                    assert abs(o.payoff_total(s, int(tot[i, j]), r) - pay[i, j]) < 1e-9
+
+
+def pin_payoff_closed_forms(o):
+    # all cooperators: every group has N_C = G = 5, payoff 5 (r - 1); all defectors: 0.
+    for r in (1.5, 3.74, 4.0, 5.0, 7.25):
+        L = 8
+        assert abs(o.payoff_groups(pattern_lattice(L, "all_c"), 3, 4, r) - 5 * (r - 1)) < 1e-12
+        assert o.payoff_groups(pattern_lattice(L, "all_d"), 3, 4, r) == 0.0
+        # the maximum count is G^2 = 25
+        assert o.group_count_total(pattern_lattice(L, "all_c"), 0, 0) == 25
+
+
+# --------------------------------------------------------------------------- #
+# Fermi rule, Eq. (3): symmetry, tie, K -> 0 and K -> inf limits, one value    #
+# --------------------------------------------------------------------------- #
+def pin_fermi_threshold(o):
+    # W(D) + W(-D) = 1, so floor(W 2^32) + floor((1-W) 2^32) is 2^32 or 2^32 - 1
+    for d in np.linspace(-12.0, 12.0, 97):
+        for K in (0.1, 0.5, 2.0):
+            t1 = o.threshold(float(d), 0.0, K)
+            t2 = o.threshold(0.0, float(d), K)
+            assert t1 + t2 in (TWO32 - 1, TWO32), (d, K, t1, t2)
+    # tie: W = 1/2 exactly
+    for a in (-3.0, 0.0, 1.6, 15.0):
+        for K in (0.01, 0.5, 100.0):
+            assert o.threshold(a, a, K) == 1 << 31
+    # K -> 0: x copies y iff Pi_y > Pi_x (Section III, after Eq. (3))
+    K0 = 1e-6
+    assert o.threshold(0.0, 0.4, K0) == TWO32 - 1
+    assert o.threshold(0.4, 0.0, K0) == 0
+    # K -> inf: a coin flip
+    t = o.threshold(-7.0, 9.0, 1e12)
+    assert abs(t - (1 << 31)) < 1 << 12
+    # the better-paid neighbour is imitated with probability above 1/2
+    assert o.threshold(1.6, -1.0, 0.5) < 1 << 31 < o.threshold(-1.0, 1.6, 0.5)
+    # one value: a defector next to a lone cooperator (payoffs 1.6 and -1.0 at
+    # r = 4, hand-worked) with K = 0.5: W = 1 / (1 + e^5.2) = 0.0054863...
+    t = o.threshold(1.6, -1.0, 0.5)
+    assert abs(t / TWO32 - 0.00548629) < 1e-7, t / TWO32
+    # monotone in Pi_y - Pi_x
+    ts = [o.threshold(0.0, float(d), 0.5) for d in np.linspace(-5, 5, 41)]
+    assert all(b >= a for a, b in zip(ts, ts[1:]))
+
+
+def pin_adoption_comparator(o):
+    # lone cooperator at (0,0); x = (0,1) a defector, y = (0,0) (direction 1: j - 1)
+    r, K = 4.0, 0.5
+    lat = pattern_lattice(8, "lone_c")
+    t = o.threshold(1.6, -1.0, K)
+    assert t > 0
+    a = lat.copy()
+    assert o.elementary_update(a, 0, 1, 1, t - 1, r, K) == 1 and a[0, 1] == 1
+    a = lat.copy()
+    assert o.elementary_update(a, 0, 1, 1, t, r, K) == 0 and a[0, 1] == 0
+    # same strategy: never changes
+    a = lat.copy()
+    assert o.elementary_update(a, 0, 3, 0, 0, r, K) == 0 and a.sum() == 1
+    # the cooperator next to three... direction codes: 0 j+1, 1 j-1, 2 i+1, 3 i-1
+    a = pattern_lattice(8, "lone_c")
+    assert o.elementary_update(a, 1, 0, 3, 0, r, K) == 1 and a[1, 0] == 1   # y = (0, 0)
+    a = pattern_lattice(8, "lone_c")
+    assert o.elementary_update(a, 7, 0, 2, 0, r, K) == 1 and a[7, 0] == 1   # y = (0, 0) wrapped
+    a = pattern_lattice(8, "lone_c")
+    assert o.elementary_update(a, 0, 7, 0, 0, r, K) == 1 and a[0, 7] == 1   # y = (0, 0) wrapped
+    a = pattern_lattice(8, "lone_c")
+    assert o.elementary_update(a, 0, 1, 0, 0, r, K) == 0                    # y = (0, 2), a D
+
+
+# --------------------------------------------------------------------------- #
+# Dynamics: initial density, absorbing states, schedule coverage, order        #
+# --------------------------------------------------------------------------- #
+def pin_init_density(o):
+    for p in (0.0, 0.2, 0.5, 0.8, 1.0):
+        lat = o.init(128, 99, p)
+        frac = lat.mean()
+        assert abs(frac - p) < 0.01, (p, frac)
+    assert o.init(64, 1, 0.5).sum() != o.init(64, 2, 0.5).sum() or \
+        not np.array_equal(o.init(64, 1, 0.5), o.init(64, 2, 0.5))
+
+
+def pin_absorbing_states(o):
+    # s_y = s_x everywhere: Eq. (3) is never applied, the lattice never changes
+    for name in ("all_c", "all_d"):
+        for seed, r, K in ((1, 3.0, 0.5), (7, 5.0, 0.1), (3, 4.2, 10.0)):
+            lat = pattern_lattice(16, name)
+            ref = lat.copy()
+            counts = o.run(lat, r, K, seed, 0, 5)
+            assert np.array_equal(lat, ref)
+            assert all(int(c) == int(ref.sum()) for c in counts)
+
+
+def pin_counts_match_lattice(o):
+    lat = o.init(32, 5, 0.5)
+    counts = o.run(lat, 4.2, 0.5, 5, 0, 3)
+    assert int(counts[-1]) == int(lat.sum())
+    assert o.count(lat) == int(lat.sum())
+
+
+def pin_schedule_coverage(o):
+    """Every site takes part: with K huge (coin-flip adoption, Section III) the
+    sixteen (i mod 4, j mod 4) classes change strategy at equal rates."""
+    L = 32
+    lat = o.init(L, 17, 0.5)
+    changes = np.zeros((L, L))
+    for k in range(16 * 24):
+        before = lat.copy()
+        o.sublattice_step(lat, 4.0, 1e9, 17, k)
+        changes += (lat != before)
+    per_class = np.array([changes[a::4, b::4].sum() for a in range(4) for b in range(4)])
+    mean = per_class.mean()
+    assert per_class.min() > 0.6 * mean, per_class
+    # and a step changes only sites of one class
+    lat2 = o.init(L, 3, 0.5)
+    before = lat2.copy()
+    o.sublattice_step(lat2, 4.0, 1e9, 3, 5)
+    diff = np.argwhere(lat2 != before)
+    assert len(diff) > 0
+    assert len({(int(i) % 4, int(j) % 4) for i, j in diff}) == 1
+
+
+def pin_order_independence(o):
+    for L, seed in ((16, 2), (40, 9)):
+        a = o.init(L, seed, 0.5)
+        b = a.copy()
+        c = a.copy()
+        ca = o.run(a, 3.9, 0.5, seed, 0, 6)
+        cb = o.run(b, 3.9, 0.5, seed, 0, 6, reverse=True)
+        cc = o.run(c, 3.9, 0.5, seed, 0, 6, threads=3)
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+        assert np.array_equal(ca, cb) and np.array_equal(ca, cc)
+
+
+def pin_stream_uniformity(o):
+    seed = 42
+    offs = np.array([o.offset(seed, k) for k in range(16 * 400)])
+    hist = np.bincount(offs, minlength=16)
+    exp = len(offs) / 16
+    chi2 = float(((hist - exp) ** 2 / exp).sum())
+    assert chi2 < 45.0, (chi2, hist)    # 15 dof, p ~ 1e-4
+    dirs = np.array([o.dir(seed, 3, a, b) for a in range(8) for b in range(128)])
+    hist = np.bincount(dirs, minlength=4)
+    chi2 = float(((hist - len(dirs) / 4) ** 2 / (len(dirs) / 4)).sum())
+    assert chi2 < 25.0, (chi2, hist)
+    us = np.array([o.u(seed, 3, a, b) for a in range(16) for b in range(64)], dtype=np.float64)
+    assert abs(us.mean() / TWO32 - 0.5) < 0.03
+
+
+# --------------------------------------------------------------------------- #
+# Statistical pins against the paper's reported physics (Section V)            #
+# --------------------------------------------------------------------------- #
+def stationary_density(o, L, r, K, seed, n_mcs, window, classic=False, threads=4):
+    lat = o.init(L, seed, 0.5)
+    if classic:
+        c = o.classic_run(lat, r, K, seed, 0, n_mcs)
+    else:
+        c = o.run(lat, r, K, seed, 0, n_mcs, threads=threads)
+    return float(c[-window:].mean()) / (L * L)
+
+
+def pin_paper_density_r398(o):
+    # Fig. 5 caption: with K = 0.5 and r = 3.98 the stationary fraction of
+    # cooperators is 1/2.
+    vals = [stationary_density(o, 128, 3.98, 0.5, s, 1200, 400) for s in (21, 22)]
+    assert abs(np.mean(vals) - 0.5) < 0.03, vals
+
+
+def pin_extinction_below_rc(o):
+    # Section V: below r_c = 3.7443 the system falls into the absorbing all-D phase.
+    for seed in (31, 32):
+        rho = stationary_density(o, 64, 3.5, 0.5, seed, 1200, 10)
+        assert rho == 0.0, rho
+    # above it cooperators survive
+    assert stationary_density(o, 64, 4.2, 0.5, 33, 600, 100) > 0.3
+
+
+def pin_schedules_agree(o):
+    # the sublattice schedule and the classic random-sequential one (Section III)
+    # give the same stationary density
+    for r in (4.5, 5.0):
+        sub = np.mean([stationary_density(o, 96, r, 0.5, s, 1000, 400) for s in (41, 42)])
+        cla = np.mean([stationary_density(o, 96, r, 0.5, s, 1000, 400, classic=True)
+                       for s in (43, 44)])
+        assert abs(sub - cla) < 0.03, (r, sub, cla)
+
+
+def pin_payoff_consistency_during_run(o):
+    o.clear_errors()
+    lat = o.init(24, 8, 0.5)
+    o.run(lat, 4.1, 0.5, 8, 0, 4)
+    assert o.errors() == 0
+
+
+FAST_PINS = [pin_philox_kat, pin_payoff_hand_worked, pin_payoff_brute_force,
+             pin_payoff_closed_forms, pin_fermi_threshold, pin_adoption_comparator,
+             pin_init_density, pin_absorbing_states, pin_counts_match_lattice,
+             pin_schedule_coverage, pin_order_independence, pin_stream_uniformity,
+             pin_payoff_consistency_during_run]
+SLOW_PINS = [pin_paper_density_r398, pin_extinction_below_rc, pin_schedules_agree]
