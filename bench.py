@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark: site updates per second of the public goods game Monte Carlo on GB300.
+
+Workload (one "step" = one full Monte Carlo step, L^2 elementary updates done as 16
+sublattice steps): the L = 8192 bit-packed lattice of the critical-decay experiment,
+K = 0.5, r = 3.744 (at the absorbing transition, r_c = 3.7443 in Section V, Fig. 4),
+Bernoulli(1/2) initial state (Section III), seed 1 (+ rank). Inputs are resident in
+HBM when the timed region starts; the L2 cache is flushed between timed steps (a
+256 MiB write that the per-step CUDA events exclude).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. ``--impl reference`` times the CPU oracle (test
+infrastructure, as it stands) on the host cores for the same metric and config.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site updates/s at L=8192 (% HBM roofline); r_c search time, surrogate vs plain"
+UNIT = "site updates/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the
+# SHA-256 of the kernel source it was taken on (reported only while that source is
+# unchanged). Filled from profiles/.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=8192)
+    ap.add_argument("--layout", default="bitpack", choices=["u8", "bitpack"])
+    ap.add_argument("--r", type=float, default=3.744)
+    ap.add_argument("--K", type=float, default=0.5)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "simple", "tiled"])
+    ap.add_argument("--fuse", type=int, default=1)
+    ap.add_argument("--tile-x", type=int, default=0)
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_1704_08098_gb300", "csrc", "pgg_kernels_tiled.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes_per_update(layout: str, k: int) -> float:
+    """Bytes a launch of k fused sublattice steps must move per site update: it reads the
+    whole lattice once and writes the N/16 updated sites (k = 1, in place) or the whole
+    lattice (k > 1, into the second buffer), for k N / 16 updates. b = bytes per site."""
+    b = 1.0 if layout == "u8" else 1.0 / 8.0
+    if k == 1:
+        return 17.0 * b
+    return 32.0 * b / k
+
+
+def cpu_baseline(L, r, K, seed, budget_s=12.0):
+    """The CPU oracle, as it stands, on this host's cores: one MCS on the same workload
+    (more if it finishes early), timed with a steady clock."""
+    import oracle
+    o = oracle.Oracle()
+    threads = os.cpu_count() or 1
+    lat = o.init(L, seed, 0.5)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.run(lat, r, K, seed, 16 * n, 1, threads=threads)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s / 2 or n >= 8:
+            break
+    return {"value": L * L * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} MCS of the L={L} workload from its Bernoulli(0.5) start "
+                      f"({n * L * L} updates, {el:.1f} s, OpenMP over the sites of a step)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    o = oracle.Oracle()
+    threads = os.cpu_count() or 1
+    L = args.L
+    lat = o.init(L, args.seed, 0.5)
+    k = 0
+    for _ in range(args.warmup):
+        o.run(lat, args.r, args.K, args.seed, k, 1, threads=threads)
+        k += 16
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.run(lat, args.r, args.K, args.seed, k, 1, threads=threads)
+        k += 16
+    el = time.perf_counter() - t0
+    value = L * L * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"L={L} PGG lattice, r={args.r}, K={args.K}, Bernoulli(0.5) "
+                               f"start, seed {args.seed}; one step = 1 MCS", "L": L,
+                   "layout": "u8 (oracle)", "r": args.r, "K": args.K},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} timed MCS after {args.warmup} warm-up MCS"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("PGG_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    from paper_1704_08098_gb300 import build, pgg
+    build.build()
+    stream = torch.cuda.current_stream()
+
+    L = args.L
+    lat = pgg.Lattice(L, args.r, args.K, layout=args.layout, stream=stream.cuda_stream)
+    if args.kernel != "auto":
+        lat.set_schedule(args.kernel, args.fuse, args.tile_x, args.tile_y)
+    sched = lat.schedule()
+    lat.seed(args.seed + rank, 0.5)
+    for _ in range(args.warmup):
+        lat.advance(1)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        lat.advance(1)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = float(L) * L * args.steps * world
+    value = updates / (total_ms / 1e3)
+
+    # dominant kernel: launches of the step kernel inside one MCS
+    k = sched["steps_per_launch"]
+    launches_per_mcs = 16 // k
+    launch_ms = (total_ms / args.steps) / launches_per_mcs
+    bpu = algorithmic_bytes_per_update(args.layout, k)
+    bytes_per_launch = bpu * (L * L / 16.0) * k
+    pk, pk_kind = peaks()
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get((src_hash, args.layout, L, k))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "peak_kind": pk_kind + " (STREAM-style copy)",
+                "kernel": f"k_step_tiled<{args.layout}> ({sched['kernel']}, k={k}, "
+                          f"tile {sched['tile_x']}x{sched['tile_y']})",
+                "algorithmic_bytes_per_update": bpu,
+                "launch_ms": launch_ms}
+
+    # end to end through the public API with host buffers: upload the lattice from pinned
+    # memory, run one MCS, read the count back
+    e2e = None
+    if not args.no_e2e:
+        host_lat, _ = lat.get()
+        pinned = torch.from_numpy(host_lat.reshape(-1)).pin_memory()
+        counts = np.zeros(1, dtype=np.uint64)
+        reps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            lat.set_from_pointer(pinned.data_ptr(), 0)
+            lat.step_mcs(1, counts)
+        el = time.perf_counter() - t0
+        e2e = {"value": L * L * reps / el, "unit": UNIT, "h2d_bytes_per_step": L * L,
+               "d2h_bytes_per_step": 8,
+               "path": "pgg_set_lattice(pinned host, L*L bytes) + pgg_step_mcs(1, host counts)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(L, args.r, args.K, args.seed)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u1" if args.layout == "bitpack" else "u8", "data": "synthetic",
+        "config": {"workload": f"L={L} {args.layout} PGG lattice, r={args.r}, K={args.K}, "
+                               f"Bernoulli(0.5) start, seed {args.seed}+rank; one step = 1 MCS "
+                               f"= {L * L} site updates",
+                   "L": L, "layout": args.layout, "r": args.r, "K": args.K,
+                   "schedule": sched, "l2": "flushed between timed steps (256 MiB write, "
+                                              "excluded by the per-step CUDA events)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_mcs * args.steps,
+        "clocks": clocks, "wall_s": wall, "step_ms": step_ms,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * pgg.h -- C ABI of the GB300 (sm_103a) library for the spatial public goods game
+ * Monte Carlo of Perc, "High-performance parallel computing in the classroom using
+ * the public goods game as an example" (arXiv:1704.08098).
+ *
+ * The model (Section III): L x L periodic square lattice, strategies C (1) and D (0);
+ * every player belongs to G = 5 overlapping groups (Fig. 1); in a group with N_C
+ * cooperators a cooperator earns r N_C / 5 - 1 and a defector r N_C / 5 (Eq. (1)-(2),
+ * c = 1); a player's payoff is the sum over its five groups. An elementary step lets a
+ * player x adopt the strategy of a random nearest neighbour y with the Fermi
+ * probability W = 1 / (1 + exp((P_x - P_y) / K)) (Eq. (3)); L^2 elementary steps are
+ * one full Monte Carlo step (MCS). The observable is the cooperator fraction rho_C
+ * (Eq. (4)).
+ *
+ * Parallel schedule: the random-sequential order of Section III is replaced by
+ * sublattice steps. Step k updates, at once, every site (i, j) with
+ * (i mod 4, j mod 4) equal to an offset drawn for step k; such sites are at least 4
+ * apart and an update reads only sites within Manhattan distance 3 (Section IV,
+ * Fig. 3), so the updates of one step are independent. 16 steps make one MCS.
+ *
+ * Randomness: Philox4x32-10 keyed by the 64-bit seed; every draw is a function of
+ * (seed, step, site), so results do not depend on the launch configuration. The
+ * counter layout is:
+ *   init    (q_lo, q_hi, 0, 1<<24), q = (i*L + j) >> 2, word (i*L + j) & 3 < floor(p 2^32)
+ *   offset  (m_lo, m_hi, 0, 2<<24), m = k >> 5, o = (word[(k>>3)&3] >> 4(k&7)) & 15,
+ *           row offset o >> 2, column offset o & 3
+ *   dir     (b >> 6, a, k_lo, k_hi | 3<<24), d = (word[(b>>4)&3] >> 2(b&15)) & 3,
+ *           d = 0: (i, j+1), 1: (i, j-1), 2: (i+1, j), 3: (i-1, j)
+ *   u       (b >> 2, a, k_lo, k_hi | 4<<24), u = word[b & 3]
+ * where (a, b) are the sublattice coordinates of site (4a + row offset, 4b + column
+ * offset) and k < 2^56 the step index. x adopts s_y iff s_x != s_y and u < T, with the
+ * threshold T = floor(W 2^32) (2^32 - 1 when W >= 1) evaluated on the host in IEEE
+ * double precision from P(s, S) = (r S)/5 - 5 s, S the sum of the cooperator counts of
+ * the player's five groups.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a pgg_status; no C++ exception crosses the ABI. On failure
+ *     pgg_last_error() returns a message for the calling thread.
+ *   - A context owns all device memory it allocates; host and device buffers passed
+ *     in are borrowed for the duration of the call only.
+ *   - Work is enqueued on the CUDA stream given to pgg_create (borrowed, not owned;
+ *     NULL = the legacy default stream). Calls are asynchronous on that stream unless
+ *     stated otherwise. A context must not be used from two threads at once.
+ *   - Lattices cross the ABI as L*L bytes, row-major, 1 = cooperator, 0 = defector.
+ */
+#ifndef PGG_H
+#define PGG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pgg_ctx pgg_ctx;
+
+typedef enum {
+    PGG_OK = 0,
+    PGG_ERR_ARG = -1,     /* invalid argument; nothing was enqueued */
+    PGG_ERR_CUDA = -2,    /* a CUDA call failed; the context may be unusable */
+    PGG_ERR_OOM = -3,     /* device or pinned-host allocation failed */
+    PGG_ERR_TIMEOUT = -4, /* a bounded device-side wait ran out; the kernel returned early */
+    PGG_ERR_STATE = -5    /* call not valid in the current state */
+} pgg_status;
+
+/* Storage of the lattice on the device. */
+typedef enum {
+    PGG_U8 = 0,      /* one byte per site, L*L bytes; needs L % 4 == 0 */
+    PGG_BITPACK = 1  /* one bit per site, 32 sites per uint32 along a row, bit b of
+                        word w = column 32w + b; needs L % 32 == 0 */
+} pgg_layout;
+
+/* Kernel family used by pgg_step_mcs. */
+typedef enum {
+    PGG_KERNEL_AUTO = 0,   /* the tuned default for (L, layout) */
+    PGG_KERNEL_SIMPLE = 1, /* one launch per sublattice step, one thread per 8 sites,
+                              operands from global memory; the plain baseline */
+    PGG_KERNEL_TILED = 2   /* shared-memory tiles with a 3k-site halo, k sublattice
+                              steps fused per launch (temporal blocking), bit-sliced
+                              group counts; k = 1 runs in place, k > 1 ping-pongs
+                              between two lattice buffers */
+} pgg_kernel;
+
+/* Create a context for one L x L lattice with synergy factor r and noise K (Section III,
+ * Eq. (1)-(3); G = 5, c = 1 fixed). Requires 4 <= L <= 32768, L % 4 == 0 (L % 32 == 0 for
+ * PGG_BITPACK), r > 0, K > 0. Allocates the lattice and the 2x26x26 uint32 adoption
+ * threshold table on the current CUDA device. The lattice starts all-defector with step 0
+ * until pgg_seed or pgg_set_lattice. *out is set to NULL on failure. */
+int pgg_create(pgg_ctx **out, int L, double r, double K, int layout, void *cuda_stream);
+
+/* Change r and K (rebuilds the threshold table; the lattice is kept). */
+int pgg_set_params(pgg_ctx *ctx, double r, double K);
+
+/* Initial condition of Section III: every site independently C with probability p
+ * (p = 0.5: "equal probability"), drawn from the Philox stream of `seed`; sets the step
+ * counter to 0 and the seed used by later steps. 0 <= p <= 1. */
+int pgg_seed(pgg_ctx *ctx, uint64_t seed, double p);
+
+/* Advance the lattice by n_mcs full Monte Carlo steps (16 * n_mcs sublattice steps).
+ * coop_per_mcs (nullable) receives n_mcs uint64 cooperator counts (numerator of
+ * Eq. (4)), the count after each MCS; it may be device memory (written
+ * asynchronously) or host memory (the call then synchronises the stream before
+ * returning). n_mcs >= 0; n_mcs == 0 is a no-op. */
+int pgg_step_mcs(pgg_ctx *ctx, int64_t n_mcs, uint64_t *coop_per_mcs);
+
+/* Number of cooperators now (numerator of Eq. (4)) into *out (host). Synchronises the
+ * context's stream; reports a device-side failure flagged by earlier kernels. */
+int pgg_count_coop(pgg_ctx *ctx, uint64_t *out);
+
+/* Copy the lattice to host_out (L*L bytes, row-major, 1 = C) and the sublattice step
+ * counter to *step_out (nullable; 16 per MCS). Synchronises the stream. */
+int pgg_get_lattice(pgg_ctx *ctx, uint8_t *host_out, uint64_t *step_out);
+
+/* Replace the lattice with host_in (L*L bytes, any non-zero byte = C) and set the step
+ * counter (for tests and exact checkpoint/resume: (lattice, seed, step, r, K) is the
+ * whole state). The seed is kept. Synchronises the stream. */
+int pgg_set_lattice(pgg_ctx *ctx, const uint8_t *host_in, uint64_t step);
+
+/* Current seed and step counter. */
+int pgg_get_state(const pgg_ctx *ctx, uint64_t *seed_out, uint64_t *step_out);
+
+/* Choose the kernel family, the number of sublattice steps fused per launch k
+ * (1, 2, 4, 8 or 16; PGG_KERNEL_TILED only) and the tile size in sites (tile_x a
+ * multiple of 64, tile_y a multiple of 4; 0 = default). PGG_KERNEL_AUTO restores the
+ * tuned default. */
+int pgg_set_schedule(pgg_ctx *ctx, int kernel, int steps_per_launch, int tile_x, int tile_y);
+
+/* The schedule pgg_step_mcs will use (after AUTO resolution). Any pointer may be NULL. */
+int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int *tile_x,
+                     int *tile_y);
+
+/* Copy the 2*26*26 adoption thresholds to host_out, index (s_x*26 + S_x)*26 + S_y with
+ * s_y = 1 - s_x (entries with s_x == s_y are never used). */
+int pgg_get_threshold_table(const pgg_ctx *ctx, uint32_t *host_out);
+
+/* Device pointer of the lattice (layout as created) and its size in bytes, for callers
+ * that hand the lattice to their own kernels on the same stream. */
+int pgg_lattice_device_ptr(pgg_ctx *ctx, void **dev_ptr, uint64_t *bytes);
+
+/* Release the context and its device memory. NULL is accepted. Synchronises the stream. */
+void pgg_destroy(pgg_ctx *ctx);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *pgg_last_error(void);
+
+/* Library version string. */
+const char *pgg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGG_H */

@@ -1,0 +1,406 @@
+// pgg_abi.cu -- the C ABI declared in include/pgg.h: context management, the host-built
+// adoption threshold table of Eq. (3), and the scheduling of the step kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pgg.h"
+#include "pgg_device.cuh"
+#include "pgg_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define PGG_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail(PGG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr uint64_t kMaxStep = (1ull << 56);
+
+// Adoption thresholds of Eq. (3) for every (s_x, S_x, S_y) with s_y = 1 - s_x:
+// P(s, S) = (r S)/5 - 5 s is the payoff summed over a player's five groups (Eq. (1)-(2),
+// c = 1, G = 5); W = 1 / (1 + exp((P_x - P_y) / K)); T = floor(W 2^32), 2^32 - 1 if W >= 1.
+// Evaluated in IEEE double precision with the host libm (compiled without contraction).
+void build_threshold_table(double r, double K, uint32_t *T) {
+    for (int sx = 0; sx < 2; ++sx) {
+        const int sy = 1 - sx;
+        for (int Sx = 0; Sx < pgg::kSRange; ++Sx) {
+            for (int Sy = 0; Sy < pgg::kSRange; ++Sy) {
+                const double px = (r * static_cast<double>(Sx)) / 5.0 - 5.0 * static_cast<double>(sx);
+                const double py = (r * static_cast<double>(Sy)) / 5.0 - 5.0 * static_cast<double>(sy);
+                const double w = 1.0 / (1.0 + std::exp((px - py) / K));
+                T[(sx * pgg::kSRange + Sx) * pgg::kSRange + Sy] =
+                    (w >= 1.0) ? 0xFFFFFFFFu : static_cast<uint32_t>(w * 4294967296.0);
+            }
+        }
+    }
+}
+
+bool is_pow2_fuse(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16; }
+
+}  // namespace
+
+struct pgg_ctx {
+    int L = 0;
+    double r = 0, K = 0;
+    int layout = PGG_U8;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    uint64_t seed = 0;
+    uint64_t step = 0;
+    void *lat = nullptr;      // current lattice
+    void *lat_alt = nullptr;  // second buffer for fused (k > 1) launches
+    size_t lat_bytes = 0;
+    uint32_t *table_d = nullptr;
+    uint32_t table_h[pgg::kTableEntries];
+    unsigned long long *counts_d = nullptr;
+    int64_t counts_cap = 0;
+    uint8_t *staging_d = nullptr;  // L*L bytes for uint8 <-> bit-packed transfers
+    int kernel = PGG_KERNEL_AUTO;
+    int k_fuse = 1;
+    int tile_x = 0, tile_y = 0;
+};
+
+namespace {
+
+// Resolved schedule: (kernel, k, tile_x, tile_y).
+struct Schedule {
+    int kernel, k, tile_x, tile_y;
+};
+
+bool tiled_supported(const pgg_ctx *c) { return c->L >= 64 && c->L % 64 == 0; }
+
+Schedule resolve_schedule(const pgg_ctx *c) {
+    Schedule s{c->kernel, c->k_fuse, c->tile_x, c->tile_y};
+    if (s.kernel == PGG_KERNEL_AUTO) {
+        if (!tiled_supported(c)) {
+            s = {PGG_KERNEL_SIMPLE, 1, 0, 0};
+        } else {
+            s.kernel = PGG_KERNEL_TILED;
+            s.k = 1;
+            s.tile_x = 0;
+            s.tile_y = 0;
+        }
+    }
+    if (s.kernel == PGG_KERNEL_TILED) {
+        if (s.tile_x <= 0) s.tile_x = c->L >= 1024 ? 1024 : c->L;
+        if (s.tile_y <= 0) s.tile_y = c->L >= 64 ? 64 : c->L;
+        if (s.tile_x > c->L) s.tile_x = c->L;
+        if (s.tile_y > c->L) s.tile_y = c->L;
+    } else {
+        s.k = 1;
+        s.tile_x = s.tile_y = 0;
+    }
+    return s;
+}
+
+int ensure_counts(pgg_ctx *c, int64_t n) {
+    if (n <= c->counts_cap) return PGG_OK;
+    int64_t cap = c->counts_cap > 0 ? c->counts_cap : 1024;
+    while (cap < n) cap *= 2;
+    if (c->counts_d) cudaFree(c->counts_d);
+    c->counts_d = nullptr;
+    c->counts_cap = 0;
+    cudaError_t e = cudaMalloc(&c->counts_d, static_cast<size_t>(cap) * sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(counts, %lld): %s", (long long)cap, cudaGetErrorString(e));
+    c->counts_cap = cap;
+    return PGG_OK;
+}
+
+int ensure_alt(pgg_ctx *c) {
+    if (c->lat_alt) return PGG_OK;
+    cudaError_t e = cudaMalloc(&c->lat_alt, c->lat_bytes);
+    if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(second lattice buffer): %s", cudaGetErrorString(e));
+    return PGG_OK;
+}
+
+int ensure_staging(pgg_ctx *c) {
+    if (c->staging_d) return PGG_OK;
+    cudaError_t e = cudaMalloc(&c->staging_d, static_cast<size_t>(c->L) * c->L);
+    if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(staging): %s", cudaGetErrorString(e));
+    return PGG_OK;
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pgg_last_error(void) { return g_last_error.c_str(); }
+
+const char *pgg_version(void) { return "pgg-gb300 0.1 (sm_103a)"; }
+
+int pgg_create(pgg_ctx **out, int L, double r, double K, int layout, void *cuda_stream) {
+    g_last_error.clear();
+    if (!out) return fail(PGG_ERR_ARG, "pgg_create: out is NULL");
+    *out = nullptr;
+    if (layout != PGG_U8 && layout != PGG_BITPACK) return fail(PGG_ERR_ARG, "pgg_create: unknown layout %d", layout);
+    if (L < 4 || L > 32768 || L % 4 != 0)
+        return fail(PGG_ERR_ARG, "pgg_create: L = %d must be a multiple of 4 in [4, 32768]", L);
+    if (layout == PGG_BITPACK && L % 32 != 0)
+        return fail(PGG_ERR_ARG, "pgg_create: bit-packed lattices need L %% 32 == 0 (L = %d)", L);
+    if (!(r > 0.0) || !std::isfinite(r)) return fail(PGG_ERR_ARG, "pgg_create: r must be > 0");
+    if (!(K > 0.0) || !std::isfinite(K)) return fail(PGG_ERR_ARG, "pgg_create: K must be > 0");
+    pgg_ctx *c = new (std::nothrow) pgg_ctx();
+    if (!c) return fail(PGG_ERR_OOM, "pgg_create: host allocation failed");
+    c->L = L;
+    c->r = r;
+    c->K = K;
+    c->layout = layout;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(PGG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    const uint64_t sites = static_cast<uint64_t>(L) * L;
+    c->lat_bytes = layout == PGG_U8 ? sites : sites / 8;
+    build_threshold_table(r, K, c->table_h);
+    if ((e = cudaMalloc(&c->lat, c->lat_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->table_d, sizeof c->table_h)) != cudaSuccess) {
+        pgg_destroy(c);
+        return fail(PGG_ERR_OOM, "pgg_create: cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpyAsync(c->table_d, c->table_h, sizeof c->table_h, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->lat, 0, c->lat_bytes, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        pgg_destroy(c);
+        return fail(PGG_ERR_CUDA, "pgg_create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return PGG_OK;
+}
+
+int pgg_set_params(pgg_ctx *c, double r, double K) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_set_params: NULL context");
+    if (!(r > 0.0) || !std::isfinite(r) || !(K > 0.0) || !std::isfinite(K))
+        return fail(PGG_ERR_ARG, "pgg_set_params: need r > 0 and K > 0");
+    PGG_CUDA(cudaSetDevice(c->device));
+    c->r = r;
+    c->K = K;
+    build_threshold_table(r, K, c->table_h);
+    // the host table is copied by value before the call returns
+    PGG_CUDA(cudaMemcpyAsync(c->table_d, c->table_h, sizeof c->table_h, cudaMemcpyHostToDevice, c->stream));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    return PGG_OK;
+}
+
+int pgg_seed(pgg_ctx *c, uint64_t seed, double p) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_seed: NULL context");
+    if (!(p >= 0.0 && p <= 1.0)) return fail(PGG_ERR_ARG, "pgg_seed: p must be in [0, 1]");
+    PGG_CUDA(cudaSetDevice(c->device));
+    uint64_t thr = p >= 1.0 ? (1ull << 32) : static_cast<uint64_t>(p * 4294967296.0);
+    PGG_CUDA(pgg::launch_init(c->layout, c->lat, c->L, seed, thr, c->stream));
+    c->seed = seed;
+    c->step = 0;
+    return PGG_OK;
+}
+
+int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_step_mcs: NULL context");
+    if (n_mcs < 0) return fail(PGG_ERR_ARG, "pgg_step_mcs: n_mcs < 0");
+    if (n_mcs == 0) return PGG_OK;
+    if (c->step + 16ull * static_cast<uint64_t>(n_mcs) >= kMaxStep)
+        return fail(PGG_ERR_ARG, "pgg_step_mcs: step counter would pass 2^56");
+    PGG_CUDA(cudaSetDevice(c->device));
+    int rc = ensure_counts(c, n_mcs);
+    if (rc) return rc;
+    const Schedule s = resolve_schedule(c);
+    if (s.kernel == PGG_KERNEL_TILED && s.k > 1 && (rc = ensure_alt(c))) return rc;
+    PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, static_cast<size_t>(n_mcs) * sizeof(unsigned long long), c->stream));
+    for (int64_t m = 0; m < n_mcs; ++m) {
+        if (s.kernel == PGG_KERNEL_SIMPLE) {
+            for (int j = 0; j < 16; ++j) {
+                PGG_CUDA(pgg::launch_step_simple(c->layout, c->lat, c->L, c->seed, c->step, c->table_d, c->stream));
+                ++c->step;
+            }
+            PGG_CUDA(pgg::launch_popcount(c->lat, c->lat_bytes, c->counts_d + m, c->stream));
+        } else {
+            for (int j = 0; j < 16; j += s.k) {
+                pgg::TiledArgs a;
+                a.src = c->lat;
+                a.dst = s.k == 1 ? c->lat : c->lat_alt;
+                a.L = c->L;
+                a.layout = c->layout;
+                a.seed = c->seed;
+                a.k0 = c->step;
+                a.steps = s.k;
+                a.tile_x = s.tile_x;
+                a.tile_y = s.tile_y;
+                a.table = c->table_d;
+                a.count_out = (j + s.k == 16) ? c->counts_d + m : nullptr;
+                PGG_CUDA(pgg::launch_step_tiled(a, c->stream));
+                if (s.k > 1) {
+                    void *t = c->lat;
+                    c->lat = c->lat_alt;
+                    c->lat_alt = t;
+                }
+                c->step += s.k;
+            }
+        }
+    }
+    if (coop_per_mcs) {
+        const size_t bytes = static_cast<size_t>(n_mcs) * sizeof(uint64_t);
+        if (is_device_pointer(coop_per_mcs)) {
+            PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToHost, c->stream));
+            PGG_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    }
+    PGG_CUDA(cudaGetLastError());
+    return PGG_OK;
+}
+
+int pgg_count_coop(pgg_ctx *c, uint64_t *out) {
+    g_last_error.clear();
+    if (!c || !out) return fail(PGG_ERR_ARG, "pgg_count_coop: NULL argument");
+    PGG_CUDA(cudaSetDevice(c->device));
+    int rc = ensure_counts(c, 1);
+    if (rc) return rc;
+    PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, sizeof(unsigned long long), c->stream));
+    PGG_CUDA(pgg::launch_popcount(c->lat, c->lat_bytes, c->counts_d, c->stream));
+    unsigned long long v = 0;
+    PGG_CUDA(cudaMemcpyAsync(&v, c->counts_d, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    *out = v;
+    return PGG_OK;
+}
+
+int pgg_get_lattice(pgg_ctx *c, uint8_t *host_out, uint64_t *step_out) {
+    g_last_error.clear();
+    if (!c || !host_out) return fail(PGG_ERR_ARG, "pgg_get_lattice: NULL argument");
+    PGG_CUDA(cudaSetDevice(c->device));
+    const size_t n = static_cast<size_t>(c->L) * c->L;
+    if (c->layout == PGG_U8) {
+        PGG_CUDA(cudaMemcpyAsync(host_out, c->lat, n, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        int rc = ensure_staging(c);
+        if (rc) return rc;
+        PGG_CUDA(pgg::launch_unpack(static_cast<const uint32_t *>(c->lat), c->staging_d, c->L, c->stream));
+        PGG_CUDA(cudaMemcpyAsync(host_out, c->staging_d, n, cudaMemcpyDeviceToHost, c->stream));
+    }
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    if (step_out) *step_out = c->step;
+    return PGG_OK;
+}
+
+int pgg_set_lattice(pgg_ctx *c, const uint8_t *host_in, uint64_t step) {
+    g_last_error.clear();
+    if (!c || !host_in) return fail(PGG_ERR_ARG, "pgg_set_lattice: NULL argument");
+    if (step >= kMaxStep) return fail(PGG_ERR_ARG, "pgg_set_lattice: step >= 2^56");
+    PGG_CUDA(cudaSetDevice(c->device));
+    const size_t n = static_cast<size_t>(c->L) * c->L;
+    if (c->layout == PGG_U8) {
+        PGG_CUDA(cudaMemcpyAsync(c->lat, host_in, n, cudaMemcpyHostToDevice, c->stream));
+        PGG_CUDA(pgg::launch_normalize(static_cast<uint8_t *>(c->lat), n, c->stream));
+    } else {
+        int rc = ensure_staging(c);
+        if (rc) return rc;
+        PGG_CUDA(cudaMemcpyAsync(c->staging_d, host_in, n, cudaMemcpyHostToDevice, c->stream));
+        PGG_CUDA(pgg::launch_pack(c->staging_d, static_cast<uint32_t *>(c->lat), c->L, c->stream));
+    }
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    c->step = step;
+    return PGG_OK;
+}
+
+int pgg_get_state(const pgg_ctx *c, uint64_t *seed_out, uint64_t *step_out) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_get_state: NULL context");
+    if (seed_out) *seed_out = c->seed;
+    if (step_out) *step_out = c->step;
+    return PGG_OK;
+}
+
+int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, int tile_y) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_set_schedule: NULL context");
+    if (kernel != PGG_KERNEL_AUTO && kernel != PGG_KERNEL_SIMPLE && kernel != PGG_KERNEL_TILED)
+        return fail(PGG_ERR_ARG, "pgg_set_schedule: unknown kernel %d", kernel);
+    if (kernel == PGG_KERNEL_TILED) {
+        if (!tiled_supported(c)) return fail(PGG_ERR_ARG, "pgg_set_schedule: the tiled kernel needs L %% 64 == 0 (L = %d)", c->L);
+        if (!is_pow2_fuse(steps_per_launch))
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: steps_per_launch must be 1, 2, 4, 8 or 16");
+        if (tile_x < 0 || tile_x % 64 != 0) return fail(PGG_ERR_ARG, "pgg_set_schedule: tile_x must be a multiple of 64");
+        if (tile_y < 0 || tile_y % 4 != 0) return fail(PGG_ERR_ARG, "pgg_set_schedule: tile_y must be a multiple of 4");
+        const int tx = tile_x == 0 ? (c->L >= 1024 ? 1024 : c->L) : (tile_x > c->L ? c->L : tile_x);
+        const int ty = tile_y == 0 ? 64 : (tile_y > c->L ? c->L : tile_y);
+        if (pgg::tiled_smem_bytes(c->layout, steps_per_launch, tx, ty) == 0)
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: tile %dx%d with %d fused steps does not fit in shared memory", tx, ty, steps_per_launch);
+    }
+    c->kernel = kernel;
+    c->k_fuse = kernel == PGG_KERNEL_TILED ? steps_per_launch : 1;
+    c->tile_x = kernel == PGG_KERNEL_TILED ? tile_x : 0;
+    c->tile_y = kernel == PGG_KERNEL_TILED ? tile_y : 0;
+    return PGG_OK;
+}
+
+int pgg_get_schedule(const pgg_ctx *c, int *kernel, int *steps_per_launch, int *tile_x, int *tile_y) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_get_schedule: NULL context");
+    const Schedule s = resolve_schedule(c);
+    if (kernel) *kernel = s.kernel;
+    if (steps_per_launch) *steps_per_launch = s.k;
+    if (tile_x) *tile_x = s.tile_x;
+    if (tile_y) *tile_y = s.tile_y;
+    return PGG_OK;
+}
+
+int pgg_get_threshold_table(const pgg_ctx *c, uint32_t *host_out) {
+    g_last_error.clear();
+    if (!c || !host_out) return fail(PGG_ERR_ARG, "pgg_get_threshold_table: NULL argument");
+    std::memcpy(host_out, c->table_h, sizeof c->table_h);
+    return PGG_OK;
+}
+
+int pgg_lattice_device_ptr(pgg_ctx *c, void **dev_ptr, uint64_t *bytes) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_lattice_device_ptr: NULL context");
+    if (dev_ptr) *dev_ptr = c->lat;
+    if (bytes) *bytes = c->lat_bytes;
+    return PGG_OK;
+}
+
+void pgg_destroy(pgg_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->lat) cudaFree(c->lat);
+    if (c->lat_alt) cudaFree(c->lat_alt);
+    if (c->table_d) cudaFree(c->table_d);
+    if (c->counts_d) cudaFree(c->counts_d);
+    if (c->staging_d) cudaFree(c->staging_d);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// pgg_internal.h -- launchers shared between the C ABI (pgg_abi.cu) and the kernel
+// translation units. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace pgg {
+
+enum Layout { kU8 = 0, kPacked = 1 };
+
+// Bernoulli(p) initial lattice from the init stream; thr = floor(p 2^32) (2^32 for p = 1).
+cudaError_t launch_init(int layout, void *lat, int L, uint64_t seed, uint64_t thr,
+                        cudaStream_t s);
+
+// One sublattice step k in place with the per-site baseline kernel.
+cudaError_t launch_step_simple(int layout, void *lat, int L, uint64_t seed, uint64_t k,
+                               const uint32_t *table, cudaStream_t s);
+
+// *out += number of set bits in buf (bytes % 16 == 0, buf 16-byte aligned). A uint8
+// lattice holds 0/1 bytes, so this counts cooperators for both layouts.
+cudaError_t launch_popcount(const void *buf, size_t bytes, unsigned long long *out,
+                            cudaStream_t s);
+
+// uint8 (0 / non-zero) <-> bit-packed conversion of an L x L lattice (L % 32 == 0).
+cudaError_t launch_pack(const uint8_t *src, uint32_t *dst, int L, cudaStream_t s);
+cudaError_t launch_unpack(const uint32_t *src, uint8_t *dst, int L, cudaStream_t s);
+
+// Map every non-zero byte to 1 (n % 16 == 0, 16-byte aligned).
+cudaError_t launch_normalize(uint8_t *buf, size_t n, cudaStream_t s);
+
+// Tiled, temporally blocked step kernel: `steps` sublattice steps k0 .. k0+steps-1.
+// src and dst may be equal only when steps == 1. If count_out is not NULL the
+// cooperator count of the result is added to *count_out.
+struct TiledArgs {
+    const void *src;
+    void *dst;
+    int L;
+    int layout;
+    uint64_t seed;
+    uint64_t k0;
+    int steps;
+    int tile_x;  // sites, multiple of 64
+    int tile_y;  // sites, multiple of 4
+    const uint32_t *table;
+    unsigned long long *count_out;
+};
+cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s);
+// Shared memory (bytes) the tiled kernel needs for a configuration; 0 if unsupported.
+size_t tiled_smem_bytes(int layout, int steps, int tile_x, int tile_y);
+
+}  // namespace pgg

@@ -1,0 +1,218 @@
+"""Thin Python binding of the C ABI in ``include/pgg.h`` (ctypes, argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libpgg.so``; this module only
+converts numpy arrays and Python numbers into the ABI's plain pointers and sizes.
+If the library has not been built, loading raises instead of falling back to
+anything else. PyTorch, when present, supplies the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libpgg.so")
+
+PGG_OK, PGG_ERR_ARG, PGG_ERR_CUDA, PGG_ERR_OOM, PGG_ERR_TIMEOUT, PGG_ERR_STATE = 0, -1, -2, -3, -4, -5
+U8, BITPACK = 0, 1
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED = 0, 1, 2
+LAYOUTS = {"u8": U8, "bitpack": BITPACK, U8: U8, BITPACK: BITPACK}
+KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED}
+
+_lib = None
+
+_vp = ctypes.c_void_p
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class PGGError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def _declare(lib):
+    sig = {
+        "pgg_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, _vp]),
+        "pgg_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
+        "pgg_seed": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
+        "pgg_step_mcs": (ctypes.c_int, [_vp, ctypes.c_int64, _vp]),
+        "pgg_count_coop": (ctypes.c_int, [_vp, _u64p]),
+        "pgg_get_lattice": (ctypes.c_int, [_vp, _u8p, _u64p]),
+        "pgg_set_lattice": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64]),
+        "pgg_get_state": (ctypes.c_int, [_vp, _u64p, _u64p]),
+        "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int]),
+        "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
+        "pgg_get_threshold_table": (ctypes.c_int, [_vp, _u32p]),
+        "pgg_lattice_device_ptr": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _u64p]),
+        "pgg_destroy": (None, [_vp]),
+        "pgg_last_error": (ctypes.c_char_p, []),
+        "pgg_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def load():
+    """Load libpgg.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing; "
+                               "run paper_1704_08098_gb300.build.build()")
+        try:  # let the library share PyTorch's CUDA runtime when torch is present
+            import torch  # noqa: F401
+        except Exception:
+            pass
+        _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def last_error() -> str:
+    return load().pgg_last_error().decode()
+
+
+def check(status: int, where: str) -> None:
+    if status != PGG_OK:
+        raise PGGError(status, where, last_error())
+
+
+def current_stream_handle() -> int:
+    """The raw cudaStream_t of PyTorch's current stream (0 without torch)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+class Lattice:
+    """One L x L lattice context (``pgg_ctx``)."""
+
+    def __init__(self, L: int, r: float, K: float, layout="u8", stream: int | None = None):
+        self.lib = load()
+        self.L = int(L)
+        self.layout = LAYOUTS[layout]
+        self.stream = current_stream_handle() if stream is None else int(stream)
+        h = _vp()
+        check(self.lib.pgg_create(ctypes.byref(h), self.L, float(r), float(K), self.layout,
+                                  _vp(self.stream)), "pgg_create")
+        self._h = h
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.pgg_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- ABI calls -------------------------------------------------------------
+    def set_params(self, r: float, K: float) -> None:
+        check(self.lib.pgg_set_params(self._h, float(r), float(K)), "pgg_set_params")
+
+    def seed(self, seed: int, p: float = 0.5) -> None:
+        check(self.lib.pgg_seed(self._h, int(seed), float(p)), "pgg_seed")
+
+    def step_mcs(self, n_mcs: int, counts: np.ndarray | int | None = None):
+        """Advance n_mcs MCS. ``counts`` may be None (no counts), a host uint64 numpy
+        array of length >= n_mcs (filled; the call synchronises), or an int device
+        pointer (filled asynchronously). With counts=None a host array is returned."""
+        if counts is None:
+            out = np.zeros(max(int(n_mcs), 1), dtype=np.uint64)
+            check(self.lib.pgg_step_mcs(self._h, int(n_mcs), out.ctypes.data), "pgg_step_mcs")
+            return out[:n_mcs]
+        if isinstance(counts, np.ndarray):
+            assert counts.dtype == np.uint64 and counts.size >= n_mcs and counts.flags.c_contiguous
+            check(self.lib.pgg_step_mcs(self._h, int(n_mcs), counts.ctypes.data), "pgg_step_mcs")
+            return counts
+        check(self.lib.pgg_step_mcs(self._h, int(n_mcs), _vp(int(counts))), "pgg_step_mcs")
+        return None
+
+    def advance(self, n_mcs: int) -> None:
+        """Advance n_mcs MCS without reading counts (asynchronous)."""
+        check(self.lib.pgg_step_mcs(self._h, int(n_mcs), None), "pgg_step_mcs")
+
+    def count(self) -> int:
+        v = ctypes.c_uint64()
+        check(self.lib.pgg_count_coop(self._h, ctypes.byref(v)), "pgg_count_coop")
+        return int(v.value)
+
+    def get(self) -> tuple[np.ndarray, int]:
+        out = np.empty((self.L, self.L), dtype=np.uint8)
+        step = ctypes.c_uint64()
+        check(self.lib.pgg_get_lattice(self._h, _ptr(out, _u8p), ctypes.byref(step)),
+              "pgg_get_lattice")
+        return out, int(step.value)
+
+    def set(self, lattice: np.ndarray, step: int = 0) -> None:
+        a = np.ascontiguousarray(lattice, dtype=np.uint8)
+        assert a.shape == (self.L, self.L)
+        check(self.lib.pgg_set_lattice(self._h, _ptr(a, _u8p), int(step)), "pgg_set_lattice")
+
+    def set_from_pointer(self, host_ptr: int, step: int = 0) -> None:
+        """pgg_set_lattice from a raw host pointer (e.g. pinned memory)."""
+        check(self.lib.pgg_set_lattice(self._h, ctypes.cast(host_ptr, _u8p), int(step)),
+              "pgg_set_lattice")
+
+    def state(self) -> tuple[int, int]:
+        seed, step = ctypes.c_uint64(), ctypes.c_uint64()
+        check(self.lib.pgg_get_state(self._h, ctypes.byref(seed), ctypes.byref(step)),
+              "pgg_get_state")
+        return int(seed.value), int(step.value)
+
+    def set_schedule(self, kernel="auto", steps_per_launch: int = 1, tile_x: int = 0,
+                     tile_y: int = 0) -> None:
+        kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        check(self.lib.pgg_set_schedule(self._h, kern, int(steps_per_launch), int(tile_x),
+                                        int(tile_y)), "pgg_set_schedule")
+
+    def schedule(self) -> dict:
+        v = [ctypes.c_int() for _ in range(4)]
+        check(self.lib.pgg_get_schedule(self._h, *[ctypes.byref(x) for x in v]),
+              "pgg_get_schedule")
+        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto"}
+        return dict(kernel=names[v[0].value], steps_per_launch=v[1].value, tile_x=v[2].value,
+                    tile_y=v[3].value)
+
+    def threshold_table(self) -> np.ndarray:
+        out = np.zeros(2 * 26 * 26, dtype=np.uint32)
+        check(self.lib.pgg_get_threshold_table(self._h, _ptr(out, _u32p)),
+              "pgg_get_threshold_table")
+        return out.reshape(2, 26, 26)
+
+    def device_ptr(self) -> tuple[int, int]:
+        p, n = _vp(), ctypes.c_uint64()
+        check(self.lib.pgg_lattice_device_ptr(self._h, ctypes.byref(p), ctypes.byref(n)),
+              "pgg_lattice_device_ptr")
+        return int(p.value or 0), int(n.value)
+
+
+def version() -> str:
+    return load().pgg_version().decode()

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol that include/*.h declares,
+and rejects invalid arguments before touching the GPU (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(pgg_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1704_08098_gb300 import build, pgg
+    build.build()
+    return pgg.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("pgg_create", "pgg_seed", "pgg_step_mcs", "pgg_count_coop", "pgg_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_argument_validation_without_gpu(lib):
+    from paper_1704_08098_gb300 import pgg
+    h = ctypes.c_void_p()
+    assert lib.pgg_create(ctypes.byref(h), 30, 4.0, 0.5, pgg.U8, None) == pgg.PGG_ERR_ARG
+    assert "multiple of 4" in pgg.last_error()
+    assert lib.pgg_create(ctypes.byref(h), 48, 4.0, 0.5, pgg.BITPACK, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_create(ctypes.byref(h), 64, -1.0, 0.5, pgg.U8, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_create(ctypes.byref(h), 64, 4.0, 0.0, pgg.U8, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_create(ctypes.byref(h), 64, 4.0, 0.5, 7, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_create(None, 64, 4.0, 0.5, pgg.U8, None) == pgg.PGG_ERR_ARG
+    assert h.value is None
+    assert lib.pgg_seed(None, 1, 0.5) == pgg.PGG_ERR_ARG
+    assert lib.pgg_step_mcs(None, 1, None) == pgg.PGG_ERR_ARG
+    lib.pgg_destroy(None)
+    assert lib.pgg_version().decode().startswith("pgg-gb300")
+
+
+def test_product_path_never_imports_the_oracle():
+    """The library and its binding must not reach the CPU oracle (no fallback)."""
+    pkg = os.path.join(ROOT, "paper_1704_08098_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            text = open(path).read()
+            assert "import oracle" not in text and "from oracle" not in text, path
+            assert "pgg_oracle" not in text and "liboracle" not in text, path

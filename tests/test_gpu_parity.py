@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle, bit for bit.
+
+Lattices, per-MCS cooperator counts and the threshold table are integer or exact
+results, so every comparison is exact equality (the threshold table is built by
+each side in IEEE double precision with the same libm, see the threshold rule in
+include/pgg.h).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_08098_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def o():
+    return oracle.Oracle()
+
+
+@pytest.fixture(scope="module")
+def pgg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1704_08098_gb300 import build, pgg as P
+    build.build()
+    return P
+
+
+def run_gpu(P, L, r, K, seed, n_mcs, layout, schedule=None, p=0.5, lattice=None, step=0):
+    with P.Lattice(L, r, K, layout=layout) as lat:
+        if schedule:
+            lat.set_schedule(**schedule)
+        if lattice is None:
+            lat.seed(seed, p)
+        else:
+            lat.seed(seed, p)
+            lat.set(lattice, step)
+        counts = lat.step_mcs(n_mcs) if n_mcs else np.zeros(0, np.uint64)
+        final, k = lat.get()
+    return final, counts, k
+
+
+def run_oracle(o, L, r, K, seed, n_mcs, p=0.5, lattice=None, step=0):
+    lat = o.init(L, seed, p) if lattice is None else np.ascontiguousarray(lattice, np.uint8).copy()
+    counts = o.run(lat, r, K, seed, step, n_mcs, threads=THREADS)
+    return lat, counts
+
+
+SCHEDULES = {
+    "simple": dict(kernel="simple"),
+    "tiled_k1": dict(kernel="tiled", steps_per_launch=1),
+    "tiled_k2": dict(kernel="tiled", steps_per_launch=2, tile_x=64, tile_y=32),
+    "tiled_k4": dict(kernel="tiled", steps_per_launch=4, tile_x=128, tile_y=64),
+    "tiled_k8": dict(kernel="tiled", steps_per_launch=8),
+    "tiled_k16": dict(kernel="tiled", steps_per_launch=16, tile_x=64, tile_y=64),
+}
+
+
+def test_threshold_table_matches_oracle(o, pgg):
+    for r, K in ((4.0, 0.5), (3.7443, 0.5), (3.98, 0.5), (5.0, 0.1), (4.2, 1e-6), (3.5, 1e6),
+                 (2.0, 3.3)):
+        with pgg.Lattice(64, r, K) as lat:
+            T = lat.threshold_table()
+        for sx in (0, 1):
+            sy = 1 - sx
+            for Sx in range(26):
+                for Sy in range(26):
+                    want = o.threshold(o.payoff_total(sx, Sx, r), o.payoff_total(sy, Sy, r), K)
+                    assert int(T[sx, Sx, Sy]) == want, (r, K, sx, Sx, Sy)
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+@pytest.mark.parametrize("L,p,seed", [(64, 0.5, 1), (96, 0.3, 7), (256, 0.5, 123), (32, 1.0, 2),
+                                      (64, 0.0, 3)])
+def test_initial_condition(o, pgg, layout, L, p, seed):
+    with pgg.Lattice(L, 4.0, 0.5, layout=layout) as lat:
+        lat.seed(seed, p)
+        got, step = lat.get()
+        count = lat.count()
+    want = o.init(L, seed, p)
+    assert step == 0
+    assert np.array_equal(got, want)
+    assert count == int(want.sum())
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+@pytest.mark.parametrize("sched", sorted(SCHEDULES))
+def test_rho_trace_L64_1000_mcs(o, pgg, layout, sched):
+    """The L = 64, r = 4, K = 0.5, seed 1 workload: rho_C(t) per MCS for 1000 MCS."""
+    w = inputs.WORKLOADS["rho_trace_L64"]
+    want_lat, want_counts = run_oracle(o, w["L"], w["r"], w["K"], w["seed"], w["n_mcs"])
+    got_lat, got_counts, k = run_gpu(pgg, w["L"], w["r"], w["K"], w["seed"], w["n_mcs"], layout,
+                                     SCHEDULES[sched])
+    assert k == 16 * w["n_mcs"]
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+@pytest.mark.parametrize("L", [4, 8, 12, 20, 36, 100])
+def test_ragged_u8_sizes_simple(o, pgg, L):
+    want_lat, want_counts = run_oracle(o, L, 3.9, 0.5, 11, 40)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 3.9, 0.5, 11, 40, "u8", dict(kernel="simple"))
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+@pytest.mark.parametrize("L", [32, 96, 160])
+def test_ragged_bitpack_sizes_simple(o, pgg, L):
+    want_lat, want_counts = run_oracle(o, L, 4.1, 0.5, 12, 30)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 4.1, 0.5, 12, 30, "bitpack", dict(kernel="simple"))
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+TILED_RAGGED = [
+    # L, tile_x, tile_y, k: tiles that do not divide L, single-tile lattices, deep fusion
+    (192, 128, 40, 1), (192, 128, 40, 2), (320, 256, 96, 4), (448, 192, 68, 8),
+    (128, 128, 128, 16), (64, 64, 4, 1), (64, 64, 8, 2), (576, 512, 100, 1),
+]
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+@pytest.mark.parametrize("L,tx,ty,k", TILED_RAGGED)
+def test_tiled_ragged_tiles(o, pgg, layout, L, tx, ty, k):
+    want_lat, want_counts = run_oracle(o, L, 3.8, 0.5, 5 + k, 12)
+    sched = dict(kernel="tiled", steps_per_launch=k, tile_x=tx, tile_y=ty)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 3.8, 0.5, 5 + k, 12, layout, sched)
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+def test_structured_inputs(o, pgg, layout):
+    """Clustered and sparse lattices set through the ABI, with a nonzero start step."""
+    for lat0, step in ((inputs.clustered_lattice(128, 12, 9, seed=4), 16 * 77),
+                       (inputs.random_lattice(128, 0.05, seed=5), 3),
+                       (inputs.random_lattice(128, 0.95, seed=6), 16 * 1000 + 5)):
+        want_lat, want_counts = run_oracle(o, 128, 3.74, 0.5, 99, 25, lattice=lat0, step=step)
+        for sched in (dict(kernel="simple"), dict(kernel="tiled", steps_per_launch=4,
+                                                  tile_x=64, tile_y=32)):
+            got_lat, got_counts, k = run_gpu(pgg, 128, 3.74, 0.5, 99, 25, layout, sched,
+                                             lattice=lat0, step=step)
+            assert k == step + 16 * 25
+            assert np.array_equal(got_counts, want_counts)
+            assert np.array_equal(got_lat, want_lat)
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+@pytest.mark.parametrize("K", [1e-6, 0.5, 1e6])
+def test_noise_limits(o, pgg, layout, K):
+    want_lat, want_counts = run_oracle(o, 128, 4.0, K, 21, 20)
+    got_lat, got_counts, _ = run_gpu(pgg, 128, 4.0, K, 21, 20, layout)
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+@pytest.mark.parametrize("p", [0.0, 1.0])
+def test_absorbing_states_stay(pgg, layout, p):
+    for sched in SCHEDULES.values():
+        final, counts, _ = run_gpu(pgg, 128, 3.9, 0.5, 8, 10, layout, sched, p=p)
+        assert final.sum() == (128 * 128 if p == 1.0 else 0)
+        assert all(int(c) == int(final.sum()) for c in counts)
+
+
+def test_zero_mcs_is_noop(pgg):
+    with pgg.Lattice(64, 4.0, 0.5) as lat:
+        lat.seed(3)
+        before, k0 = lat.get()
+        lat.step_mcs(0)
+        after, k1 = lat.get()
+    assert k0 == k1 == 0 and np.array_equal(before, after)
+
+
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+def test_checkpoint_resume_is_exact(pgg, layout):
+    with pgg.Lattice(256, 3.9, 0.5, layout=layout) as a:
+        a.seed(77)
+        ca = a.step_mcs(40)
+        full, ka = a.get()
+    with pgg.Lattice(256, 3.9, 0.5, layout=layout) as b:
+        b.seed(77)
+        c1 = b.step_mcs(20)
+        mid, kmid = b.get()
+    with pgg.Lattice(256, 3.9, 0.5, layout=layout) as c:
+        c.seed(77)
+        c.set(mid, kmid)
+        c2 = c.step_mcs(20)
+        end, kc = c.get()
+    assert ka == kc and np.array_equal(full, end)
+    assert np.array_equal(ca, np.concatenate([c1, c2]))
+
+
+def test_layouts_and_schedules_agree_L1024(pgg):
+    ref = None
+    for layout in ("u8", "bitpack"):
+        for sched in SCHEDULES.values():
+            final, counts, _ = run_gpu(pgg, 1024, 3.8, 0.5, 31, 6, layout, sched)
+            if ref is None:
+                ref = (final, counts)
+            assert np.array_equal(final, ref[0]) and np.array_equal(counts, ref[1])
+
+
+def test_counts_into_device_memory(pgg):
+    import torch
+    with pgg.Lattice(128, 4.0, 0.5, layout="bitpack") as lat:
+        lat.seed(5)
+        dev = torch.zeros(30, dtype=torch.int64, device="cuda")
+        lat.step_mcs(30, dev.data_ptr())
+        torch.cuda.synchronize()
+        d = dev.cpu().numpy().astype(np.uint64)
+    with pgg.Lattice(128, 4.0, 0.5, layout="bitpack") as lat:
+        lat.seed(5)
+        h = lat.step_mcs(30)
+    assert np.array_equal(d, h)
+
+
+@pytest.mark.parametrize("L,n_mcs,layout", [(4096, 3, "u8"), (4096, 3, "bitpack"),
+                                            (8192, 2, "bitpack"), (8192, 1, "u8")])
+def test_full_size_against_oracle(o, pgg, L, n_mcs, layout):
+    """The paper's large lattices (Section V: up to 4096; 8192 here) in the default
+    (tuned) launch configuration, the one the benchmark times."""
+    want_lat, want_counts = run_oracle(o, L, 3.744, 0.5, 1, n_mcs)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 3.744, 0.5, 1, n_mcs, layout)
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
