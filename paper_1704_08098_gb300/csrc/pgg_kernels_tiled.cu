@@ -28,7 +28,7 @@ namespace {
 constexpr uint32_t kNib = 0x11111111u;
 constexpr uint32_t kLowNib = 0x0F0F0F0Fu;
 constexpr int kMaxSteps = 16;
-constexpr size_t kMaxSmem = 227 * 1024;
+constexpr size_t kMaxSmem = 227 * 1024 - 1024;  // leave room for static shared memory
 
 struct TiledParams {
     const void *src;
@@ -365,15 +365,23 @@ size_t smem_bytes_for(int steps, int tile_x, int tile_y, int wpt) {
 template <int LAYOUT, int WPT>
 cudaError_t launch_instance(const TiledParams &p, size_t smem, int grid, cudaStream_t s) {
     constexpr int kBlock = 256;
-    static bool configured = false;  // per instance; the attribute is per function
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_tiled<LAYOUT, WPT, kBlock>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(kMaxSmem));
+    auto kernel = k_step_tiled<LAYOUT, WPT, kBlock>;
+    // the opt-in limit covers static plus dynamic shared memory; raise the dynamic
+    // limit of this instance only as far as a launch needs
+    static size_t configured = 48 * 1024;
+    if (smem > configured) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
         if (e != cudaSuccess) return e;
-        configured = true;
+        if (smem + fa.sharedSizeBytes > static_cast<size_t>(optin)) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
     }
-    k_step_tiled<LAYOUT, WPT, kBlock><<<grid, kBlock, smem, s>>>(p);
+    kernel<<<grid, kBlock, smem, s>>>(p);
     return cudaGetLastError();
 }
 
