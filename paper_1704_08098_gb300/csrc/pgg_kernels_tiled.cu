@@ -40,6 +40,8 @@ struct TiledParams {
     int tiles_x, tiles_y;
     int H, hw;     // halo in sites (3 steps) and in words
     int pitch;     // physical words per shared-memory row
+    int dir_slot;  // uint16 entries of one step's direction buffer
+    int dir_words; // uint32 words reserved for the two direction buffers
     const uint32_t *table;
     unsigned long long *count_out;
 };
@@ -171,29 +173,88 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     return flips;
 }
 
+// Periodic wrap of an index that may be a few periods outside [0, m).
+__device__ __forceinline__ int wrap_small(int v, int m) {
+    while (v < 0) v += m;
+    while (v >= m) v -= m;
+    return v;
+}
+
+// The part of the tile one fused step updates: sublattice rows r_first, r_first + 4, ...
+// below row_hi, and local words [w_lo, w_hi) (sites outside [col_lo, col_hi) masked).
+struct StepGeom {
+    int row_hi, col_lo, col_hi, w_lo, w_hi, r_first, n_srows, n_words;
+};
+
+__device__ __forceinline__ StepGeom step_geom(const TiledParams &p, int ih, int iw, int j, int oi) {
+    StepGeom g;
+    const int e = 3 * (p.steps - 1 - j);
+    const int row_lo = p.H - e;
+    g.row_hi = p.H + ih + e;
+    g.col_lo = 32 * p.hw - e;
+    g.col_hi = 32 * p.hw + iw + e;
+    g.w_lo = g.col_lo >> 5;
+    g.w_hi = (g.col_hi + 31) >> 5;
+    g.r_first = row_lo + ((oi + p.H - row_lo) & 3);
+    g.n_srows = g.r_first < g.row_hi ? (g.row_hi - g.r_first + 3) >> 2 : 0;
+    g.n_words = g.w_hi - g.w_lo;
+    return g;
+}
+
+// Direction codes of step j for every unit of its region, into s_dir[srow * n_words + w]
+// (16 bits per unit). One Philox call covers 64 sublattice sites = 8 words of a row, so a
+// thread takes one row and one run of 8 words aligned to the global call boundary.
+__device__ __forceinline__ void tile_dirs(const TiledParams &p, uint16_t *s_dir, int y0, int x0w,
+                                          int ih, int iw, int j, int oi, int tid, int nthreads) {
+    const StepGeom g = step_geom(p, ih, iw, j, oi);
+    const uint64_t k = p.k0 + j;
+    const int u_lo = x0w - p.hw + g.w_lo;          // unwrapped global word of w_lo
+    const int c_lo = u_lo >> 3;                     // floor: first call-aligned run
+    const int c_hi = (x0w - p.hw + g.w_hi - 1) >> 3;
+    const int n_runs = c_hi - c_lo + 1;
+    for (int t = tid; t < g.n_srows * n_runs; t += nthreads) {
+        const int sr = t / n_runs;
+        const int c = c_lo + (t - sr * n_runs);
+        const int r = g.r_first + 4 * sr;
+        const uint32_t a = static_cast<uint32_t>(wrap_small(y0 - p.H + r, p.L) >> 2);
+        const int w0 = max(g.w_lo, 8 * c - (x0w - p.hw));
+        const int w1 = min(g.w_hi, 8 * c + 8 - (x0w - p.hw));
+        int cached = -1;
+        uint4 call = make_uint4(0, 0, 0, 0);
+        for (int w = w0; w < w1; ++w) {
+            const int gw = wrap_small(x0w - p.hw + w, p.Lw);
+            const int dg = gw >> 3;
+            if (dg != cached) {
+                call = philox4x32_10(static_cast<uint32_t>(dg), a, static_cast<uint32_t>(k),
+                                     static_cast<uint32_t>(k >> 32) | kTagDir,
+                                     static_cast<uint32_t>(p.seed), static_cast<uint32_t>(p.seed >> 32));
+                cached = dg;
+            }
+            s_dir[sr * g.n_words + (w - g.w_lo)] =
+                static_cast<uint16_t>(word_of(call, (gw >> 1) & 3) >> (16 * (gw & 1)));
+        }
+    }
+}
+
 // One sublattice step over the update region of the tile, for column offset OJ.
 template <int LAYOUT, int WPT, int BLOCK, int OJ>
 __device__ __forceinline__ void tile_step(const TiledParams &p, uint32_t *s_tile,
-                                          const uint32_t *__restrict__ s_table, int y0, int x0w,
+                                          const uint32_t *__restrict__ s_table,
+                                          const uint16_t *__restrict__ s_dir, int y0, int x0w,
                                           int ih, int iw, int j, int oi) {
     const uint64_t k = p.k0 + j;
-    const int e = 3 * (p.steps - 1 - j);
-    const int row_lo = p.H - e, row_hi = p.H + ih + e;
-    const int col_lo = 32 * p.hw - e, col_hi = 32 * p.hw + iw + e;
-    const int w_lo = col_lo >> 5, w_hi = (col_hi + 31) >> 5;
-    const int r_first = row_lo + ((oi + p.H - row_lo) & 3);
-    const int n_srows = r_first < row_hi ? (row_hi - r_first + 3) >> 2 : 0;
-    const int n_wg = (w_hi - w_lo + WPT - 1) / WPT;
-    const int n_tasks = n_srows * n_wg;
+    const StepGeom g = step_geom(p, ih, iw, j, oi);
+    const int n_wg = (g.n_words + WPT - 1) / WPT;
+    const int n_tasks = g.n_srows * n_wg;
     const bool in_place = (p.steps == 1);
 
     for (int t = threadIdx.x; t < n_tasks; t += BLOCK) {
         const int sr = t / n_wg;
         const int wg = t - sr * n_wg;
-        const int r = r_first + 4 * sr;
-        const int wa = w_lo + wg * WPT;
-        const int wb = min(wa + WPT, w_hi);
-        const int grow = mod_pos(y0 - p.H + r, p.L);
+        const int r = g.r_first + 4 * sr;
+        const int wa = g.w_lo + wg * WPT;
+        const int wb = min(wa + WPT, g.w_hi);
+        const int grow = wrap_small(y0 - p.H + r, p.L);
         UnitCtx u;
         u.seed = p.seed;
         u.k = k;
@@ -206,40 +267,31 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, uint32_t *s_tile
             wl[q] = row0[q * p.pitch + skew<WPT>(wa - 1)];
             wc[q] = row0[q * p.pitch + skew<WPT>(wa)];
         }
-        int dcall_idx = -1;
-        uint4 dcall = make_uint4(0, 0, 0, 0);
+        int gw = wrap_small(x0w - p.hw + wa, p.Lw);
 #pragma unroll
         for (int s = 0; s < WPT; ++s) {
             const int w = wa + s;
             if (w >= wb) break;
 #pragma unroll
             for (int q = 0; q < 7; ++q) wr[q] = row0[q * p.pitch + skew<WPT>(w + 1)];
-            u.gw = mod_pos(x0w - p.hw + w, p.Lw);
-            const int dci = u.gw >> 3;
-            if (dci != dcall_idx) {
-                dcall = philox4x32_10(static_cast<uint32_t>(dci), u.a, static_cast<uint32_t>(k),
-                                      static_cast<uint32_t>(k >> 32) | kTagDir,
-                                      static_cast<uint32_t>(p.seed), static_cast<uint32_t>(p.seed >> 32));
-                dcall_idx = dci;
-            }
-            u.d16 = (word_of(dcall, (u.gw >> 1) & 3) >> (16 * (u.gw & 1))) & 0xFFFFu;
+            u.gw = gw;
+            u.d16 = s_dir[sr * g.n_words + (w - g.w_lo)];
             u.msk = kNib;
-            if (w == w_lo || w == w_hi - 1) {
+            if (w == g.w_lo || w == g.w_hi - 1) {
                 // sites at local columns 32 w + OJ + 4 m inside [col_lo, col_hi)
                 const int base = 32 * w + OJ;
-                u.msk = nibble_range((col_lo - base + 3) >> 2, (col_hi - base + 3) >> 2);
+                u.msk = nibble_range((g.col_lo - base + 3) >> 2, (g.col_hi - base + 3) >> 2);
             }
             uint32_t sx;
             const uint32_t flips = unit_flips<OJ>(wl, wc, wr, u, s_table, sx);
             if (flips) {
-                const uint32_t fw = flips << OJ;
-                const uint32_t nw = wc[3] ^ fw;
+                const uint32_t nw = wc[3] ^ (flips << OJ);
                 s_tile[r * p.pitch + skew<WPT>(w)] = nw;
                 if (in_place) {
                     if (LAYOUT == kPacked) {
-                        static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + u.gw] = nw;
+                        static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + gw] = nw;
                     } else {
-                        uint8_t *rowp = static_cast<uint8_t *>(p.dst) + static_cast<size_t>(grow) * p.L + 32 * u.gw + OJ;
+                        uint8_t *rowp = static_cast<uint8_t *>(p.dst) + static_cast<size_t>(grow) * p.L + 32 * gw + OJ;
                         const uint32_t newbits = (sx ^ flips);
 #pragma unroll
                         for (int m = 0; m < 8; ++m)
@@ -252,6 +304,7 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, uint32_t *s_tile
                 wl[q] = wc[q];
                 wc[q] = wr[q];
             }
+            if (++gw == p.Lw) gw = 0;
         }
     }
 }
@@ -261,8 +314,11 @@ __global__ void __launch_bounds__(BLOCK) k_step_tiled(const TiledParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *s_table = smem;
     int *s_off = reinterpret_cast<int *>(smem + kTableEntries);
-    uint32_t *s_tile = smem + kTableEntries + kMaxSteps;
+    uint16_t *s_dir = reinterpret_cast<uint16_t *>(smem + kTableEntries + kMaxSteps);
+    uint32_t *s_tile = smem + kTableEntries + kMaxSteps + p.dir_words;
     __shared__ unsigned long long s_warp_count[BLOCK / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = BLOCK / 32;
 
     for (int t = threadIdx.x; t < kTableEntries; t += BLOCK) s_table[t] = p.table[t];
     if (threadIdx.x < p.steps) s_off[threadIdx.x] = draw_offset(p.seed, p.k0 + threadIdx.x);
@@ -276,65 +332,70 @@ __global__ void __launch_bounds__(BLOCK) k_step_tiled(const TiledParams p) {
         const int x0w = x0 >> 5;
         const int R = ih + 2 * p.H;
         const int Wr = (iw >> 5) + 2 * p.hw;
-        __syncthreads();
+        __syncthreads();  // offsets ready; the previous tile is fully consumed
         // stage tile + halo as bit rows
-        for (int idx = threadIdx.x; idx < R * Wr; idx += BLOCK) {
-            const int r = idx / Wr;
-            const int w = idx - r * Wr;
-            const int grow = mod_pos(y0 - p.H + r, p.L);
-            const int gw = mod_pos(x0w - p.hw + w, p.Lw);
-            uint32_t bits;
-            if (LAYOUT == kPacked) {
-                bits = static_cast<const uint32_t *>(p.src)[static_cast<size_t>(grow) * p.Lw + gw];
-            } else {
-                const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(p.src) +
-                                                                   static_cast<size_t>(grow) * p.L + 32 * gw);
-                bits = pack32(src[0], src[1]);
+        for (int r = warp; r < R; r += kWarps) {
+            const int grow = wrap_small(y0 - p.H + r, p.L);
+            for (int w = lane; w < Wr; w += 32) {
+                const int gw = wrap_small(x0w - p.hw + w, p.Lw);
+                uint32_t bits;
+                if (LAYOUT == kPacked) {
+                    bits = static_cast<const uint32_t *>(p.src)[static_cast<size_t>(grow) * p.Lw + gw];
+                } else {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(p.src) +
+                                                                       static_cast<size_t>(grow) * p.L + 32 * gw);
+                    bits = pack32(src[0], src[1]);
+                }
+                s_tile[r * p.pitch + skew<WPT>(w)] = bits;
             }
-            s_tile[r * p.pitch + skew<WPT>(w)] = bits;
         }
+        tile_dirs(p, s_dir, y0, x0w, ih, iw, 0, s_off[0] >> 2, threadIdx.x, BLOCK);
         __syncthreads();
         for (int j = 0; j < p.steps; ++j) {
             const int o = s_off[j];
             const int oi = o >> 2;
+            const uint16_t *dir_j = s_dir + (j & 1) * p.dir_slot;
             switch (o & 3) {
-                case 0: tile_step<LAYOUT, WPT, BLOCK, 0>(p, s_tile, s_table, y0, x0w, ih, iw, j, oi); break;
-                case 1: tile_step<LAYOUT, WPT, BLOCK, 1>(p, s_tile, s_table, y0, x0w, ih, iw, j, oi); break;
-                case 2: tile_step<LAYOUT, WPT, BLOCK, 2>(p, s_tile, s_table, y0, x0w, ih, iw, j, oi); break;
-                default: tile_step<LAYOUT, WPT, BLOCK, 3>(p, s_tile, s_table, y0, x0w, ih, iw, j, oi); break;
+                case 0: tile_step<LAYOUT, WPT, BLOCK, 0>(p, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                case 1: tile_step<LAYOUT, WPT, BLOCK, 1>(p, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                case 2: tile_step<LAYOUT, WPT, BLOCK, 2>(p, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                default: tile_step<LAYOUT, WPT, BLOCK, 3>(p, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
             }
+            if (j + 1 < p.steps)
+                tile_dirs(p, s_dir + ((j + 1) & 1) * p.dir_slot, y0, x0w, ih, iw, j + 1,
+                          s_off[j + 1] >> 2, threadIdx.x, BLOCK);
             __syncthreads();
         }
         // write the interior back (fused launches) and count it
         unsigned long long cnt = 0;
         const int iwords = iw >> 5;
-        for (int idx = threadIdx.x; idx < ih * iwords; idx += BLOCK) {
-            const int rr = idx / iwords;
-            const int ww = idx - rr * iwords;
-            const uint32_t bits = s_tile[(p.H + rr) * p.pitch + skew<WPT>(p.hw + ww)];
-            cnt += __popc(bits);
-            if (p.steps > 1) {
-                const int grow = y0 + rr;
-                const int gw = x0w + ww;
-                if (LAYOUT == kPacked) {
-                    static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + gw] = bits;
-                } else {
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.dst) +
-                                                           static_cast<size_t>(grow) * p.L + 32 * gw);
-                    dst[0] = make_uint4(bytes_of_nibble(bits), bytes_of_nibble(bits >> 4),
-                                        bytes_of_nibble(bits >> 8), bytes_of_nibble(bits >> 12));
-                    dst[1] = make_uint4(bytes_of_nibble(bits >> 16), bytes_of_nibble(bits >> 20),
-                                        bytes_of_nibble(bits >> 24), bytes_of_nibble(bits >> 28));
+        for (int rr = warp; rr < ih; rr += kWarps) {
+            for (int ww = lane; ww < iwords; ww += 32) {
+                const uint32_t bits = s_tile[(p.H + rr) * p.pitch + skew<WPT>(p.hw + ww)];
+                cnt += __popc(bits);
+                if (p.steps > 1) {
+                    const int grow = y0 + rr;
+                    const int gw = x0w + ww;
+                    if (LAYOUT == kPacked) {
+                        static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + gw] = bits;
+                    } else {
+                        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.dst) +
+                                                               static_cast<size_t>(grow) * p.L + 32 * gw);
+                        dst[0] = make_uint4(bytes_of_nibble(bits), bytes_of_nibble(bits >> 4),
+                                            bytes_of_nibble(bits >> 8), bytes_of_nibble(bits >> 12));
+                        dst[1] = make_uint4(bytes_of_nibble(bits >> 16), bytes_of_nibble(bits >> 20),
+                                            bytes_of_nibble(bits >> 24), bytes_of_nibble(bits >> 28));
+                    }
                 }
             }
         }
         if (p.count_out) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-            if ((threadIdx.x & 31) == 0) s_warp_count[threadIdx.x >> 5] = cnt;
+            if (lane == 0) s_warp_count[warp] = cnt;
             __syncthreads();
             if (threadIdx.x < 32) {
-                cnt = threadIdx.x < BLOCK / 32 ? s_warp_count[threadIdx.x] : 0ull;
+                cnt = threadIdx.x < kWarps ? s_warp_count[threadIdx.x] : 0ull;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
                 if (threadIdx.x == 0 && cnt) atomicAdd(p.count_out, cnt);
@@ -343,23 +404,32 @@ __global__ void __launch_bounds__(BLOCK) k_step_tiled(const TiledParams p) {
     }
 }
 
-int pick_wpt(int tile_x) {
-    const int words = tile_x / 32;
-    return words >= 8 ? 8 : (words >= 4 ? 4 : 2);
-}
-
 int pitch_for(int wpt, int Wr) {
     int pitch = Wr + (Wr + wpt - 1) / wpt;
     if ((pitch & 1) == 0) ++pitch;
     return pitch;
 }
 
-size_t smem_bytes_for(int steps, int tile_x, int tile_y, int wpt) {
+// Largest region of one step: sublattice rows and words (for the direction buffer).
+void dir_slot_dims(int steps, int tile_x, int tile_y, int *srows, int *words) {
+    const int e = 3 * (steps - 1);
+    *srows = (tile_y + 2 * e + 3) / 4 + 1;
+    *words = (tile_x + 2 * e + 31) / 32 + 2;
+}
+
+size_t smem_bytes_for(int steps, int tile_x, int tile_y, int wpt, int *dir_slot, int *dir_words) {
     const int H = 3 * steps;
     const int hw = halo_words(steps);
     const int R = tile_y + 2 * H;
     const int Wr = tile_x / 32 + 2 * hw;
-    return sizeof(uint32_t) * (static_cast<size_t>(kTableEntries) + kMaxSteps + static_cast<size_t>(R) * pitch_for(wpt, Wr));
+    int sr, ww;
+    dir_slot_dims(steps, tile_x, tile_y, &sr, &ww);
+    const int slot = sr * ww;                       // uint16 entries per step slot
+    const int dwords = (2 * slot + 1) / 2 + 1;      // two slots, in uint32 words
+    if (dir_slot) *dir_slot = slot;
+    if (dir_words) *dir_words = (dwords + 3) & ~3;  // keep the tile 16-byte aligned
+    return sizeof(uint32_t) * (static_cast<size_t>(kTableEntries) + kMaxSteps + ((dwords + 3) & ~3) +
+                               static_cast<size_t>(R) * pitch_for(wpt, Wr));
 }
 
 template <int LAYOUT, int WPT>
@@ -385,12 +455,18 @@ cudaError_t launch_instance(const TiledParams &p, size_t smem, int grid, cudaStr
     return cudaGetLastError();
 }
 
+// Words per thread task: small tiles need small tasks to keep all threads busy.
+int pick_wpt(int tile_x, int tile_y) {
+    const long tasks_wpt2 = static_cast<long>(tile_y / 4) * (tile_x / 64);
+    return tasks_wpt2 >= 512 ? 2 : 1;
+}
+
 }  // namespace
 
 size_t tiled_smem_bytes(int layout, int steps, int tile_x, int tile_y) {
     (void)layout;
     if (steps < 1 || steps > kMaxSteps || tile_x < 64 || tile_x % 64 || tile_y < 4 || tile_y % 4) return 0;
-    const size_t b = smem_bytes_for(steps, tile_x, tile_y, pick_wpt(tile_x));
+    const size_t b = smem_bytes_for(steps, tile_x, tile_y, pick_wpt(tile_x, tile_y), nullptr, nullptr);
     return b <= kMaxSmem ? b : 0;
 }
 
@@ -412,21 +488,19 @@ cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s) {
     p.tiles_y = (a.L + a.tile_y - 1) / a.tile_y;
     p.H = 3 * a.steps;
     p.hw = halo_words(a.steps);
-    const int wpt = pick_wpt(a.tile_x);
+    const int wpt = pick_wpt(a.tile_x, a.tile_y);
     p.pitch = pitch_for(wpt, a.tile_x / 32 + 2 * p.hw);
     p.table = a.table;
     p.count_out = a.count_out;
-    const size_t smem = smem_bytes_for(a.steps, a.tile_x, a.tile_y, wpt);
+    const size_t smem = smem_bytes_for(a.steps, a.tile_x, a.tile_y, wpt, &p.dir_slot, &p.dir_words);
     if (smem > kMaxSmem) return cudaErrorInvalidValue;
     const int grid = p.tiles_x * p.tiles_y;
     if (a.layout == kPacked) {
-        if (wpt == 8) return launch_instance<kPacked, 8>(p, smem, grid, s);
-        if (wpt == 4) return launch_instance<kPacked, 4>(p, smem, grid, s);
-        return launch_instance<kPacked, 2>(p, smem, grid, s);
+        if (wpt == 2) return launch_instance<kPacked, 2>(p, smem, grid, s);
+        return launch_instance<kPacked, 1>(p, smem, grid, s);
     }
-    if (wpt == 8) return launch_instance<kU8, 8>(p, smem, grid, s);
-    if (wpt == 4) return launch_instance<kU8, 4>(p, smem, grid, s);
-    return launch_instance<kU8, 2>(p, smem, grid, s);
+    if (wpt == 2) return launch_instance<kU8, 2>(p, smem, grid, s);
+    return launch_instance<kU8, 1>(p, smem, grid, s);
 }
 
 }  // namespace pgg
