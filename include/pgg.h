@@ -137,6 +137,28 @@ int pgg_get_threshold_table(const pgg_ctx *ctx, uint32_t *host_out);
  * that hand the lattice to their own kernels on the same stream. */
 int pgg_lattice_device_ptr(pgg_ctx *ctx, void **dev_ptr, uint64_t *bytes);
 
+/* Allocation-free variant of pgg_step_mcs, for callers that cannot allocate device memory
+ * (code running inside CUDA-graph capture or a host callback, plug-ins whose host
+ * application owns all device memory, services that must not allocate after start-up).
+ * The paper has no counterpart; it is a packaging of the fused tiled kernel.
+ *   lattice_in, lattice_out: device buffers in `layout` (PGG_U8: L*L bytes; PGG_BITPACK:
+ *     L*L/8 bytes, see pgg_layout); they may be the same buffer.
+ *   Runs n_mcs MCS of the model with (r, K, seed) starting at sublattice step step0
+ *   (the state (lattice, seed, step, r, K) is the same as that of a context).
+ *   coop_per_mcs: NULL or a device buffer of n_mcs uint64 counts; it is cleared and filled.
+ *   Requires L % 64 == 0, 64 <= L, and a lattice of at most 4 MiB (L <= 2048 for PGG_U8,
+ *   L <= 4096 for PGG_BITPACK); larger sizes return PGG_ERR_ARG with a message.
+ * It calls no cudaMalloc, cudaFree or allocating routine: its scratch (a 4 MiB intermediate
+ * lattice plus the threshold table) is one fixed device array in the library, held by every
+ * GPU that loads the library until the process exits. The first call on a device resolves
+ * that array's address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture. All calls share the array: calls that overlap on the GPU (on
+ * different streams or devices' contexts sharing it) race and must be serialised by the
+ * caller. Asynchronous on cuda_stream. */
+int pgg_step_mcs_noalloc(const void *lattice_in, void *lattice_out, int L, int layout, double r,
+                         double K, uint64_t seed, uint64_t step0, int64_t n_mcs,
+                         uint64_t *coop_per_mcs, void *cuda_stream);
+
 /* Release the context and its device memory. NULL is accepted. Synchronises the stream. */
 void pgg_destroy(pgg_ctx *ctx);
 

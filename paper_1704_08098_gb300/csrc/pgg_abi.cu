@@ -13,6 +13,29 @@
 #include "pgg_device.cuh"
 #include "pgg_internal.h"
 
+namespace pgg {
+
+// Adoption thresholds of Eq. (3) for every (s_x, S_x, S_y) with s_y = 1 - s_x:
+// P(s, S) = (r S)/5 - 5 s is the payoff summed over a player's five groups (Eq. (1)-(2),
+// c = 1, G = 5); W = 1 / (1 + exp((P_x - P_y) / K)); T = floor(W 2^32), 2^32 - 1 if W >= 1.
+// Evaluated in IEEE double precision with the host libm (compiled without contraction).
+void build_threshold_table(double r, double K, uint32_t *T) {
+    for (int sx = 0; sx < 2; ++sx) {
+        const int sy = 1 - sx;
+        for (int Sx = 0; Sx < pgg::kSRange; ++Sx) {
+            for (int Sy = 0; Sy < pgg::kSRange; ++Sy) {
+                const double px = (r * static_cast<double>(Sx)) / 5.0 - 5.0 * static_cast<double>(sx);
+                const double py = (r * static_cast<double>(Sy)) / 5.0 - 5.0 * static_cast<double>(sy);
+                const double w = 1.0 / (1.0 + std::exp((px - py) / K));
+                T[(sx * pgg::kSRange + Sx) * pgg::kSRange + Sy] =
+                    (w >= 1.0) ? 0xFFFFFFFFu : static_cast<uint32_t>(w * 4294967296.0);
+            }
+        }
+    }
+}
+
+}  // namespace pgg
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -35,28 +58,20 @@ int fail(int code, const char *fmt, ...) {
 
 constexpr uint64_t kMaxStep = (1ull << 56);
 
-// Adoption thresholds of Eq. (3) for every (s_x, S_x, S_y) with s_y = 1 - s_x:
-// P(s, S) = (r S)/5 - 5 s is the payoff summed over a player's five groups (Eq. (1)-(2),
-// c = 1, G = 5); W = 1 / (1 + exp((P_x - P_y) / K)); T = floor(W 2^32), 2^32 - 1 if W >= 1.
-// Evaluated in IEEE double precision with the host libm (compiled without contraction).
-void build_threshold_table(double r, double K, uint32_t *T) {
-    for (int sx = 0; sx < 2; ++sx) {
-        const int sy = 1 - sx;
-        for (int Sx = 0; Sx < pgg::kSRange; ++Sx) {
-            for (int Sy = 0; Sy < pgg::kSRange; ++Sy) {
-                const double px = (r * static_cast<double>(Sx)) / 5.0 - 5.0 * static_cast<double>(sx);
-                const double py = (r * static_cast<double>(Sy)) / 5.0 - 5.0 * static_cast<double>(sy);
-                const double w = 1.0 / (1.0 + std::exp((px - py) / K));
-                T[(sx * pgg::kSRange + Sx) * pgg::kSRange + Sy] =
-                    (w >= 1.0) ? 0xFFFFFFFFu : static_cast<uint32_t>(w * 4294967296.0);
-            }
-        }
-    }
-}
-
 bool is_pow2_fuse(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16; }
 
 }  // namespace
+
+namespace pgg {
+
+int record_error(int code, const char *message) {
+    g_last_error = message;
+    return code;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+}  // namespace pgg
 
 struct pgg_ctx {
     int L = 0;
@@ -181,7 +196,7 @@ int pgg_create(pgg_ctx **out, int L, double r, double K, int layout, void *cuda_
     }
     const uint64_t sites = static_cast<uint64_t>(L) * L;
     c->lat_bytes = layout == PGG_U8 ? sites : sites / 8;
-    build_threshold_table(r, K, c->table_h);
+    pgg::build_threshold_table(r, K, c->table_h);
     if ((e = cudaMalloc(&c->lat, c->lat_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&c->table_d, sizeof c->table_h)) != cudaSuccess) {
         pgg_destroy(c);
@@ -205,7 +220,7 @@ int pgg_set_params(pgg_ctx *c, double r, double K) {
     PGG_CUDA(cudaSetDevice(c->device));
     c->r = r;
     c->K = K;
-    build_threshold_table(r, K, c->table_h);
+    pgg::build_threshold_table(r, K, c->table_h);
     // the host table is copied by value before the call returns
     PGG_CUDA(cudaMemcpyAsync(c->table_d, c->table_h, sizeof c->table_h, cudaMemcpyHostToDevice, c->stream));
     PGG_CUDA(cudaStreamSynchronize(c->stream));

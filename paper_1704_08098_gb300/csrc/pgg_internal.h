@@ -11,6 +11,14 @@ namespace pgg {
 
 enum Layout { kU8 = 0, kPacked = 1 };
 
+// Host-built adoption thresholds of Eq. (3), 2*26*26 entries indexed
+// (s_x*26 + S_x)*26 + S_y (defined in pgg_abi.cu).
+void build_threshold_table(double r, double K, uint32_t *T);
+
+// Set / clear the calling thread's pgg_last_error() message (defined in pgg_abi.cu).
+int record_error(int code, const char *message);
+void clear_error();
+
 // Bernoulli(p) initial lattice from the init stream; thr = floor(p 2^32) (2^32 for p = 1).
 cudaError_t launch_init(int layout, void *lat, int L, uint64_t seed, uint64_t thr,
                         cudaStream_t s);

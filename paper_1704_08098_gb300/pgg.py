@@ -52,6 +52,9 @@ def _declare(lib):
         "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
         "pgg_get_threshold_table": (ctypes.c_int, [_vp, _u32p]),
         "pgg_lattice_device_ptr": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _u64p]),
+        "pgg_step_mcs_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                ctypes.c_uint64, ctypes.c_int64, _vp, _vp]),
         "pgg_destroy": (None, [_vp]),
         "pgg_last_error": (ctypes.c_char_p, []),
         "pgg_version": (ctypes.c_char_p, []),
@@ -212,6 +215,19 @@ class Lattice:
         check(self.lib.pgg_lattice_device_ptr(self._h, ctypes.byref(p), ctypes.byref(n)),
               "pgg_lattice_device_ptr")
         return int(p.value or 0), int(n.value)
+
+
+def step_mcs_noalloc(lattice_in: int, lattice_out: int, L: int, layout, r: float, K: float,
+                     seed: int, step0: int, n_mcs: int, counts_dev: int | None = None,
+                     stream: int | None = None) -> None:
+    """pgg_step_mcs_noalloc on raw device pointers (see include/pgg.h): for callers that
+    cannot allocate device memory; the library's fixed scratch array is used instead."""
+    lib = load()
+    st = current_stream_handle() if stream is None else int(stream)
+    check(lib.pgg_step_mcs_noalloc(_vp(int(lattice_in)), _vp(int(lattice_out)), int(L),
+                                   LAYOUTS[layout], float(r), float(K), int(seed), int(step0),
+                                   int(n_mcs), _vp(int(counts_dev)) if counts_dev else None,
+                                   _vp(st)), "pgg_step_mcs_noalloc")
 
 
 def version() -> str:
