@@ -75,10 +75,13 @@ typedef enum {
     PGG_KERNEL_AUTO = 0,   /* the tuned default for (L, layout) */
     PGG_KERNEL_SIMPLE = 1, /* one launch per sublattice step, one thread per 8 sites,
                               operands from global memory; the plain baseline */
-    PGG_KERNEL_TILED = 2   /* shared-memory tiles with a 3k-site halo, k sublattice
-                              steps fused per launch (temporal blocking), bit-sliced
-                              group counts; k = 1 runs in place, k > 1 ping-pongs
-                              between two lattice buffers */
+    PGG_KERNEL_TILED = 2,  /* shared-memory tiles with a 3k-site halo, k sublattice
+                              steps fused per launch (temporal blocking); k = 1 runs in
+                              place, k > 1 ping-pongs between two lattice buffers */
+    PGG_KERNEL_DIRECT = 3  /* bit-packed lattices with L % 256 == 0 only: one launch per
+                              sublattice step, in place, operands straight from global
+                              memory, tile_x = words per thread (4 or 8); the cooperator
+                              count is carried as a running total */
 } pgg_kernel;
 
 /* Create a context for one L x L lattice with synergy factor r and noise K (Section III,
@@ -121,7 +124,8 @@ int pgg_get_state(const pgg_ctx *ctx, uint64_t *seed_out, uint64_t *step_out);
 
 /* Choose the kernel family, the number of sublattice steps fused per launch k
  * (1, 2, 4, 8 or 16; PGG_KERNEL_TILED only) and the tile size in sites (tile_x a
- * multiple of 64, tile_y a multiple of 4; 0 = default). PGG_KERNEL_AUTO restores the
+ * multiple of 64, tile_y a multiple of 4; 0 = default); for PGG_KERNEL_DIRECT tile_x is
+ * the number of words per thread (4 or 8, 0 = default). PGG_KERNEL_AUTO restores the
  * tuned default. */
 int pgg_set_schedule(pgg_ctx *ctx, int kernel, int steps_per_launch, int tile_x, int tile_y);
 

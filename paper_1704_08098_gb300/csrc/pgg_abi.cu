@@ -92,6 +92,8 @@ struct pgg_ctx {
     int kernel = PGG_KERNEL_AUTO;
     int k_fuse = 1;
     int tile_x = 0, tile_y = 0;
+    unsigned long long *running_d = nullptr;  // cooperator count carried by the direct kernel
+    bool running_valid = false;               // running_d equals the lattice's count
 };
 
 namespace {
@@ -106,7 +108,9 @@ bool tiled_supported(const pgg_ctx *c) { return c->L >= 64 && c->L % 64 == 0; }
 Schedule resolve_schedule(const pgg_ctx *c) {
     Schedule s{c->kernel, c->k_fuse, c->tile_x, c->tile_y};
     if (s.kernel == PGG_KERNEL_AUTO) {
-        if (!tiled_supported(c)) {
+        if (pgg::direct_supported(c->layout, c->L)) {
+            s = {PGG_KERNEL_DIRECT, 1, 8, 0};
+        } else if (!tiled_supported(c)) {
             s = {PGG_KERNEL_SIMPLE, 1, 0, 0};
         } else {
             s.kernel = PGG_KERNEL_TILED;
@@ -114,6 +118,12 @@ Schedule resolve_schedule(const pgg_ctx *c) {
             s.tile_x = 0;
             s.tile_y = 0;
         }
+    }
+    if (s.kernel == PGG_KERNEL_DIRECT) {
+        s.k = 1;
+        if (s.tile_x != 4 && s.tile_x != 8) s.tile_x = 8;
+        s.tile_y = 0;
+        return s;
     }
     if (s.kernel == PGG_KERNEL_TILED) {
         if (s.tile_x <= 0) s.tile_x = c->L >= 1024 ? 1024 : c->L;
@@ -236,6 +246,7 @@ int pgg_seed(pgg_ctx *c, uint64_t seed, double p) {
     PGG_CUDA(pgg::launch_init(c->layout, c->lat, c->L, seed, thr, c->stream));
     c->seed = seed;
     c->step = 0;
+    c->running_valid = false;
     return PGG_OK;
 }
 
@@ -252,8 +263,30 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     const Schedule s = resolve_schedule(c);
     if (s.kernel == PGG_KERNEL_TILED && s.k > 1 && (rc = ensure_alt(c))) return rc;
     PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, static_cast<size_t>(n_mcs) * sizeof(unsigned long long), c->stream));
+    if (s.kernel == PGG_KERNEL_DIRECT) {
+        if (!c->running_d) {
+            cudaError_t e = cudaMalloc(&c->running_d, sizeof(unsigned long long));
+            if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(running count): %s", cudaGetErrorString(e));
+            c->running_valid = false;
+        }
+        if (!c->running_valid) {
+            PGG_CUDA(cudaMemsetAsync(c->running_d, 0, sizeof(unsigned long long), c->stream));
+            PGG_CUDA(pgg::launch_popcount(c->lat, c->lat_bytes, c->running_d, c->stream));
+            c->running_valid = true;
+        }
+    } else {
+        c->running_valid = false;
+    }
     for (int64_t m = 0; m < n_mcs; ++m) {
-        if (s.kernel == PGG_KERNEL_SIMPLE) {
+        if (s.kernel == PGG_KERNEL_DIRECT) {
+            for (int j = 0; j < 16; ++j) {
+                PGG_CUDA(pgg::launch_step_direct(static_cast<uint32_t *>(c->lat), c->L, c->seed, c->step, c->table_d,
+                                                 c->running_d, s.tile_x, c->stream));
+                ++c->step;
+            }
+            PGG_CUDA(cudaMemcpyAsync(c->counts_d + m, c->running_d, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        } else if (s.kernel == PGG_KERNEL_SIMPLE) {
             for (int j = 0; j < 16; ++j) {
                 PGG_CUDA(pgg::launch_step_simple(c->layout, c->lat, c->L, c->seed, c->step, c->table_d, c->stream));
                 ++c->step;
@@ -346,6 +379,7 @@ int pgg_set_lattice(pgg_ctx *c, const uint8_t *host_in, uint64_t step) {
     }
     PGG_CUDA(cudaStreamSynchronize(c->stream));
     c->step = step;
+    c->running_valid = false;
     return PGG_OK;
 }
 
@@ -360,8 +394,20 @@ int pgg_get_state(const pgg_ctx *c, uint64_t *seed_out, uint64_t *step_out) {
 int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, int tile_y) {
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_set_schedule: NULL context");
-    if (kernel != PGG_KERNEL_AUTO && kernel != PGG_KERNEL_SIMPLE && kernel != PGG_KERNEL_TILED)
+    if (kernel != PGG_KERNEL_AUTO && kernel != PGG_KERNEL_SIMPLE && kernel != PGG_KERNEL_TILED &&
+        kernel != PGG_KERNEL_DIRECT)
         return fail(PGG_ERR_ARG, "pgg_set_schedule: unknown kernel %d", kernel);
+    if (kernel == PGG_KERNEL_DIRECT) {
+        if (!pgg::direct_supported(c->layout, c->L))
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: the direct kernel needs a bit-packed lattice with L %% 256 == 0");
+        if (tile_x != 0 && tile_x != 4 && tile_x != 8)
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: direct kernel words per thread must be 4 or 8");
+        c->kernel = kernel;
+        c->k_fuse = 1;
+        c->tile_x = tile_x;
+        c->tile_y = 0;
+        return PGG_OK;
+    }
     if (kernel == PGG_KERNEL_TILED) {
         if (!tiled_supported(c)) return fail(PGG_ERR_ARG, "pgg_set_schedule: the tiled kernel needs L %% 64 == 0 (L = %d)", c->L);
         if (!is_pow2_fuse(steps_per_launch))
@@ -415,6 +461,7 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->table_d) cudaFree(c->table_d);
     if (c->counts_d) cudaFree(c->counts_d);
     if (c->staging_d) cudaFree(c->staging_d);
+    if (c->running_d) cudaFree(c->running_d);
     delete c;
 }
 

@@ -43,6 +43,48 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Round keys of Philox4x32-10 for one seed: round r uses (k0 + r W0, k1 + r W1). Built once
+// on the host and passed in kernel parameters, so that every round reads its key as a
+// constant operand instead of recomputing it.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_round_keys(uint64_t seed) {
+    PhiloxKeys rk;
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = k0;
+        rk.k1[r] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ void philox_round(uint4 &c, uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+}
+
+// Philox4x32-10 with precomputed round keys.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const PhiloxKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) philox_round(c, rk.k0[r], rk.k1[r]);
+    return c;
+}
+
+// Two independent counters, rounds interleaved for instruction-level parallelism.
+__device__ __forceinline__ void philox_rk2(uint4 &a, uint4 &b, const PhiloxKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        philox_round(a, rk.k0[r], rk.k1[r]);
+        philox_round(b, rk.k0[r], rk.k1[r]);
+    }
+}
+
 __device__ __forceinline__ uint32_t word_of(const uint4 &w, int idx) {
     return idx == 0 ? w.x : idx == 1 ? w.y : idx == 2 ? w.z : w.w;
 }

@@ -17,9 +17,9 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libpgg.so")
 
 PGG_OK, PGG_ERR_ARG, PGG_ERR_CUDA, PGG_ERR_OOM, PGG_ERR_TIMEOUT, PGG_ERR_STATE = 0, -1, -2, -3, -4, -5
 U8, BITPACK = 0, 1
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED = 0, 1, 2
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, KERNEL_DIRECT = 0, 1, 2, 3
 LAYOUTS = {"u8": U8, "bitpack": BITPACK, U8: U8, BITPACK: BITPACK}
-KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED}
+KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED, "direct": KERNEL_DIRECT}
 
 _lib = None
 
@@ -200,7 +200,7 @@ class Lattice:
         v = [ctypes.c_int() for _ in range(4)]
         check(self.lib.pgg_get_schedule(self._h, *[ctypes.byref(x) for x in v]),
               "pgg_get_schedule")
-        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto"}
+        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto", KERNEL_DIRECT: "direct"}
         return dict(kernel=names[v[0].value], steps_per_launch=v[1].value, tile_x=v[2].value,
                     tile_y=v[3].value)
 

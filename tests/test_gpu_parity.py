@@ -230,3 +230,41 @@ def test_full_size_against_oracle(o, pgg, L, n_mcs, layout):
     got_lat, got_counts, _ = run_gpu(pgg, L, 3.744, 0.5, 1, n_mcs, layout)
     assert np.array_equal(got_counts, want_counts)
     assert np.array_equal(got_lat, want_lat)
+
+
+DIRECT = {"direct4": dict(kernel="direct", tile_x=4), "direct8": dict(kernel="direct", tile_x=8)}
+
+
+@pytest.mark.parametrize("sched", sorted(DIRECT))
+@pytest.mark.parametrize("L", [256, 768, 1024])
+def test_direct_kernel(o, pgg, sched, L):
+    want_lat, want_counts = run_oracle(o, L, 3.9, 0.5, 40 + L, 15)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 3.9, 0.5, 40 + L, 15, "bitpack", DIRECT[sched])
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+def test_direct_kernel_structured_and_switching(o, pgg):
+    """Set lattices mid-run and alternate kernels: the running cooperator count of the
+    direct kernel must be re-established whenever another path changed the lattice."""
+    L = 512
+    lat0 = inputs.clustered_lattice(L, 30, 14, seed=9)
+    ref = lat0.copy()
+    want = []
+    k = 16 * 5
+    for n in (3, 2, 4):
+        want.append(o.run(ref, 3.75, 0.5, 7, k, n, threads=THREADS))
+        k += 16 * n
+    with pgg.Lattice(L, 3.75, 0.5, layout="bitpack") as lat:
+        lat.seed(7)
+        lat.set(lat0, 16 * 5)
+        lat.set_schedule("direct", 1, 4)
+        c1 = lat.step_mcs(3)
+        lat.set_schedule("tiled", 2, 128, 64)
+        c2 = lat.step_mcs(2)
+        lat.set_schedule("direct", 1, 8)
+        c3 = lat.step_mcs(4)
+        got, step = lat.get()
+    assert step == k
+    assert np.array_equal(np.concatenate([c1, c2, c3]), np.concatenate(want))
+    assert np.array_equal(got, ref)
