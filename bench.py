@@ -33,10 +33,14 @@ UNIT = "site updates/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by the
-# SHA-256 of the kernel source it was taken on (reported only while that source is
-# unchanged). Filled from profiles/.
-NCU_TRAFFIC = {}
+# Per-launch counters of the dominant kernel from one ncu capture of this benchmark (see
+# profiles/), keyed by the kernel's source file hash and launch configuration; they are used
+# only while that source is unchanged. alu_warp_inst = ALU-pipe warp instructions,
+# dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
+NCU = {}
+
+# Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
+ALU_LANES_PER_SM_CLOCK = 64
 
 
 def parse():
@@ -50,12 +54,13 @@ def parse():
     ap.add_argument("--r", type=float, default=3.744)
     ap.add_argument("--K", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "simple", "tiled"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "simple", "tiled", "direct"])
     ap.add_argument("--fuse", type=int, default=1)
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -74,9 +79,13 @@ def peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def kernel_source_hash() -> str:
-    p = os.path.join(ROOT, "paper_1704_08098_gb300", "csrc", "pgg_kernels_tiled.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+def kernel_source_hash(kernel: str) -> str:
+    names = {"direct": ["pgg_kernels_direct.cu"], "tiled": ["pgg_kernels_tiled.cu"],
+             "simple": ["pgg_kernels_basic.cu"]}[kernel] + ["pgg_unit.cuh", "pgg_device.cuh"]
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_1704_08098_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -226,10 +235,13 @@ def main():
 
     L = args.L
     lat = pgg.Lattice(L, args.r, args.K, layout=args.layout, stream=stream.cuda_stream)
+    lat.seed(args.seed + rank, 0.5)
+    tuned = None
     if args.kernel != "auto":
         lat.set_schedule(args.kernel, args.fuse, args.tile_x, args.tile_y)
+    elif not args.no_autotune:
+        tuned = lat.autotune(3)  # untimed; restores the lattice and step counter
     sched = lat.schedule()
-    lat.seed(args.seed + rank, 0.5)
     for _ in range(args.warmup):
         lat.advance(1)
     torch.cuda.synchronize()
@@ -264,23 +276,40 @@ def main():
     updates = float(L) * L * args.steps * world
     value = updates / (total_ms / 1e3)
 
-    # dominant kernel: launches of the step kernel inside one MCS
+    # dominant kernel: the step kernel, 16 / k launches per MCS; its launch duration is the
+    # MCS time / launches (includes launch gaps, so it understates the kernel's own rate)
     k = sched["steps_per_launch"]
     launches_per_mcs = 16 // k
-    launch_ms = (total_ms / args.steps) / launches_per_mcs
-    bpu = algorithmic_bytes_per_update(args.layout, k)
-    bytes_per_launch = bpu * (L * L / 16.0) * k
+    launch_s = (total_ms / args.steps) / launches_per_mcs / 1e3
+    updates_per_launch = L * L / 16.0 * k
     pk, pk_kind = peaks()
-    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
-    src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get((src_hash, args.layout, L, k))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                "peak_kind": pk_kind + " (STREAM-style copy)",
-                "kernel": f"k_step_tiled<{args.layout}> ({sched['kernel']}, k={k}, "
-                          f"tile {sched['tile_x']}x{sched['tile_y']})",
-                "algorithmic_bytes_per_update": bpu,
-                "launch_ms": launch_ms}
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0
+    key = f"{sched['kernel']}:{kernel_source_hash(sched['kernel'])}:{args.layout}:{L}:" \
+          f"{k}:{sched['tile_x']}:{sched['tile_y']}"
+    ncu = NCU.get(key)
+    alu_peak = sm_count * ALU_LANES_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12  # Tops/s
+    bpu = algorithmic_bytes_per_update(args.layout, k)
+    hbm_achieved = bpu * updates_per_launch / launch_s / 1e9
+    hbm_model = {"algorithmic_bytes_per_update": bpu, "achieved_gbs": hbm_achieved,
+                 "peak_gbs": pk["hbm_gbs"], "frac": hbm_achieved / pk["hbm_gbs"],
+                 "peak_kind": pk_kind}
+    if ncu is not None:
+        achieved = ncu["alu_warp_inst"] * 32 / launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                    "frac": achieved / alu_peak, "traffic": ncu["dram_bytes"],
+                    "peak_kind": f"derived: {sm_count} SMs x {ALU_LANES_PER_SM_CLOCK} ALU lanes/clk"
+                                 f" x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
+                    "work_per_launch": f"{ncu['alu_warp_inst']} ALU-pipe warp instructions "
+                                       f"(ncu, {updates_per_launch:.0f} updates)"}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": hbm_achieved / pk["hbm_gbs"], "traffic": None,
+                    "peak_kind": pk_kind + " (STREAM-style copy); no ncu counters for this "
+                                 "kernel source yet"}
+    roofline.update({"kernel": f"{sched['kernel']} (k={k}, tile {sched['tile_x']}x"
+                               f"{sched['tile_y']})", "launch_ms": launch_s * 1e3,
+                     "ncu_key": key, "hbm_model": hbm_model})
 
     # end to end through the public API with host buffers: upload the lattice from pinned
     # memory, run one MCS, read the count back
@@ -313,7 +342,8 @@ def main():
                                f"Bernoulli(0.5) start, seed {args.seed}+rank; one step = 1 MCS "
                                f"= {L * L} site updates",
                    "L": L, "layout": args.layout, "r": args.r, "K": args.K,
-                   "schedule": sched, "l2": "flushed between timed steps (256 MiB write, "
+                   "schedule": sched, "autotuned": tuned,
+                   "l2": "flushed between timed steps (256 MiB write, "
                                               "excluded by the per-step CUDA events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

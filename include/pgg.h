@@ -80,8 +80,9 @@ typedef enum {
                               place, k > 1 ping-pongs between two lattice buffers */
     PGG_KERNEL_DIRECT = 3  /* bit-packed lattices with L % 256 == 0 only: one launch per
                               sublattice step, in place, operands straight from global
-                              memory, tile_x = words per thread (4 or 8); the cooperator
-                              count is carried as a running total */
+                              memory, tile_x = words per thread (4 or 8), tile_y = threads
+                              per block (64, 128 or 256); the cooperator count is carried as
+                              a running total */
 } pgg_kernel;
 
 /* Create a context for one L x L lattice with synergy factor r and noise K (Section III,
@@ -125,9 +126,19 @@ int pgg_get_state(const pgg_ctx *ctx, uint64_t *seed_out, uint64_t *step_out);
 /* Choose the kernel family, the number of sublattice steps fused per launch k
  * (1, 2, 4, 8 or 16; PGG_KERNEL_TILED only) and the tile size in sites (tile_x a
  * multiple of 64, tile_y a multiple of 4; 0 = default); for PGG_KERNEL_DIRECT tile_x is
- * the number of words per thread (4 or 8, 0 = default). PGG_KERNEL_AUTO restores the
- * tuned default. */
+ * the number of words per thread (4 or 8) and tile_y the block size (64, 128, 256), 0 =
+ * default. PGG_KERNEL_AUTO restores the tuned default. */
 int pgg_set_schedule(pgg_ctx *ctx, int kernel, int steps_per_launch, int tile_x, int tile_y);
+
+/* Autotuner: time every applicable schedule (direct words-per-thread x block size, tiled
+ * k x tile shape, simple) for n_mcs MCS (1..1000) on a saved copy of this context's lattice,
+ * restore the lattice, step counter and the caller's schedule, and remember the fastest
+ * schedule for (device, L, layout) in a process-wide table that PGG_KERNEL_AUTO consults
+ * from then on (for every context with that device, L and layout). The winner and its time
+ * per MCS are returned through the (nullable) pointers. Synchronises the stream; allocates
+ * one lattice-sized temporary. Results do not depend on the schedule. */
+int pgg_autotune(pgg_ctx *ctx, int n_mcs, int *kernel, int *steps_per_launch, int *tile_x,
+                 int *tile_y, float *ms_per_mcs);
 
 /* The schedule pgg_step_mcs will use (after AUTO resolution). Any pointer may be NULL. */
 int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int *tile_x,

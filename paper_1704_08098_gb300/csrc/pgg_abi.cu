@@ -6,8 +6,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "pgg.h"
 #include "pgg_device.cuh"
@@ -105,11 +109,24 @@ struct Schedule {
 
 bool tiled_supported(const pgg_ctx *c) { return c->L >= 64 && c->L % 64 == 0; }
 
+// Schedules chosen by pgg_autotune, per (device, L, layout); consulted by PGG_KERNEL_AUTO.
+std::mutex g_tuned_mutex;
+std::map<std::tuple<int, int, int>, Schedule> g_tuned;
+
+bool tuned_lookup(const pgg_ctx *c, Schedule *out) {
+    std::lock_guard<std::mutex> lock(g_tuned_mutex);
+    auto it = g_tuned.find(std::make_tuple(c->device, c->L, c->layout));
+    if (it == g_tuned.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 Schedule resolve_schedule(const pgg_ctx *c) {
     Schedule s{c->kernel, c->k_fuse, c->tile_x, c->tile_y};
+    if (s.kernel == PGG_KERNEL_AUTO && tuned_lookup(c, &s)) return s;
     if (s.kernel == PGG_KERNEL_AUTO) {
         if (pgg::direct_supported(c->layout, c->L)) {
-            s = {PGG_KERNEL_DIRECT, 1, 8, 0};
+            s = {PGG_KERNEL_DIRECT, 1, 8, 256};
         } else if (!tiled_supported(c)) {
             s = {PGG_KERNEL_SIMPLE, 1, 0, 0};
         } else {
@@ -122,7 +139,7 @@ Schedule resolve_schedule(const pgg_ctx *c) {
     if (s.kernel == PGG_KERNEL_DIRECT) {
         s.k = 1;
         if (s.tile_x != 4 && s.tile_x != 8) s.tile_x = 8;
-        s.tile_y = 0;
+        if (s.tile_y != 64 && s.tile_y != 128 && s.tile_y != 256) s.tile_y = 256;
         return s;
     }
     if (s.kernel == PGG_KERNEL_TILED) {
@@ -281,7 +298,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         if (s.kernel == PGG_KERNEL_DIRECT) {
             for (int j = 0; j < 16; ++j) {
                 PGG_CUDA(pgg::launch_step_direct(static_cast<uint32_t *>(c->lat), c->L, c->seed, c->step, c->table_d,
-                                                 c->running_d, s.tile_x, c->stream));
+                                                 c->running_d, s.tile_x, s.tile_y, c->stream));
                 ++c->step;
             }
             PGG_CUDA(cudaMemcpyAsync(c->counts_d + m, c->running_d, sizeof(unsigned long long),
@@ -402,10 +419,12 @@ int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, i
             return fail(PGG_ERR_ARG, "pgg_set_schedule: the direct kernel needs a bit-packed lattice with L %% 256 == 0");
         if (tile_x != 0 && tile_x != 4 && tile_x != 8)
             return fail(PGG_ERR_ARG, "pgg_set_schedule: direct kernel words per thread must be 4 or 8");
+        if (tile_y != 0 && tile_y != 64 && tile_y != 128 && tile_y != 256)
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: direct kernel block size must be 64, 128 or 256");
         c->kernel = kernel;
         c->k_fuse = 1;
         c->tile_x = tile_x;
-        c->tile_y = 0;
+        c->tile_y = tile_y;
         return PGG_OK;
     }
     if (kernel == PGG_KERNEL_TILED) {
@@ -449,6 +468,95 @@ int pgg_lattice_device_ptr(pgg_ctx *c, void **dev_ptr, uint64_t *bytes) {
     if (!c) return fail(PGG_ERR_ARG, "pgg_lattice_device_ptr: NULL context");
     if (dev_ptr) *dev_ptr = c->lat;
     if (bytes) *bytes = c->lat_bytes;
+    return PGG_OK;
+}
+
+int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int *tile_x, int *tile_y,
+                 float *ms_per_mcs) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_autotune: NULL context");
+    if (n_mcs < 1 || n_mcs > 1000) return fail(PGG_ERR_ARG, "pgg_autotune: n_mcs must be in [1, 1000]");
+    PGG_CUDA(cudaSetDevice(c->device));
+    // candidates
+    std::vector<Schedule> cand;
+    if (pgg::direct_supported(c->layout, c->L))
+        for (int upt : {4, 8})
+            for (int blk : {64, 128, 256}) cand.push_back({PGG_KERNEL_DIRECT, 1, upt, blk});
+    if (tiled_supported(c)) {
+        const int tiles[][2] = {{2048, 128}, {1024, 256}, {1024, 128}, {1024, 64}, {512, 128}, {512, 64},
+                                {256, 64}, {256, 32}, {128, 32}, {128, 16}, {64, 16}, {64, 8}};
+        for (int k : {1, 2, 4, 8})
+            for (const auto &t : tiles) {
+                if (t[0] > c->L || t[1] > c->L) continue;
+                if (pgg::tiled_smem_bytes(c->layout, k, t[0], t[1]) == 0) continue;
+                cand.push_back({PGG_KERNEL_TILED, k, t[0], t[1]});
+            }
+    }
+    cand.push_back({PGG_KERNEL_SIMPLE, 1, 0, 0});
+    // trials run on the context's own buffers from a saved copy of the state
+    void *saved = nullptr;
+    cudaError_t e = cudaMalloc(&saved, c->lat_bytes);
+    if (e != cudaSuccess) return fail(PGG_ERR_OOM, "pgg_autotune: cudaMalloc(saved lattice): %s", cudaGetErrorString(e));
+    const uint64_t step0 = c->step;
+    const int kern0 = c->kernel, k0 = c->k_fuse, tx0 = c->tile_x, ty0 = c->tile_y;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Schedule best{PGG_KERNEL_SIMPLE, 1, 0, 0};
+    float best_ms = 1e30f;
+    int rc = PGG_OK;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(saved, c->lat, c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) {
+        rc = fail(PGG_ERR_CUDA, "pgg_autotune: %s", cudaGetErrorString(e));
+    }
+    for (size_t i = 0; rc == PGG_OK && i < cand.size(); ++i) {
+        const Schedule &s = cand[i];
+        c->kernel = s.kernel;
+        c->k_fuse = s.k;
+        c->tile_x = s.tile_x;
+        c->tile_y = s.tile_y;
+        float ms = 0;
+        for (int rep = 0; rep < 2 && rc == PGG_OK; ++rep) {  // rep 0 warms up
+            if ((e = cudaMemcpyAsync(c->lat, saved, c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) {
+                rc = fail(PGG_ERR_CUDA, "pgg_autotune: restore: %s", cudaGetErrorString(e));
+                break;
+            }
+            c->step = step0;
+            c->running_valid = false;
+            if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { rc = fail(PGG_ERR_CUDA, "pgg_autotune: %s", cudaGetErrorString(e)); break; }
+            rc = pgg_step_mcs(c, n_mcs, nullptr);
+            if (rc) break;
+            if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+                rc = fail(PGG_ERR_CUDA, "pgg_autotune: timing: %s", cudaGetErrorString(e));
+        }
+        if (rc == PGG_OK && ms / n_mcs < best_ms) {
+            best_ms = ms / n_mcs;
+            best = s;
+        }
+    }
+    // restore the state and the caller's schedule
+    if (saved) {
+        cudaMemcpyAsync(c->lat, saved, c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(saved);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->step = step0;
+    c->running_valid = false;
+    c->kernel = kern0;
+    c->k_fuse = k0;
+    c->tile_x = tx0;
+    c->tile_y = ty0;
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mutex);
+        g_tuned[std::make_tuple(c->device, c->L, c->layout)] = best;
+    }
+    if (kernel) *kernel = best.kernel;
+    if (steps_per_launch) *steps_per_launch = best.k;
+    if (tile_x) *tile_x = best.tile_x;
+    if (tile_y) *tile_y = best.tile_y;
+    if (ms_per_mcs) *ms_per_mcs = best_ms;
     return PGG_OK;
 }
 

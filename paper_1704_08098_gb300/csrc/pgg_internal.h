@@ -58,11 +58,11 @@ struct TiledArgs {
 cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s);
 
 // In-place single sublattice step k on a bit-packed lattice with operands read from global
-// memory, upt (4 or 8) words per thread; *running (if not NULL) += the change in the number
-// of cooperators. Needs L % 256 == 0.
+// memory, upt (4 or 8) words per thread, blocks of `block` (64, 128 or 256) threads;
+// *running (if not NULL) += the change in the number of cooperators. Needs L % 256 == 0.
 bool direct_supported(int layout, int L);
 cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
-                               unsigned long long *running, int upt, cudaStream_t s);
+                               unsigned long long *running, int upt, int block, cudaStream_t s);
 // Shared memory (bytes) the tiled kernel needs for a configuration; 0 if unsupported.
 size_t tiled_smem_bytes(int layout, int steps, int tile_x, int tile_y);
 

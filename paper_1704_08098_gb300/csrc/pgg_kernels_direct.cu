@@ -18,6 +18,11 @@
 #include "pgg_internal.h"
 #include "pgg_unit.cuh"
 
+// Minimum resident CTAs per SM requested from the register allocator.
+#ifndef PGG_DIRECT_MIN_BLOCKS
+#define PGG_DIRECT_MIN_BLOCKS 1
+#endif
+
 namespace pgg {
 namespace {
 
@@ -60,7 +65,8 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
         u.k = p.k;
         u.a = static_cast<uint32_t>(a);
         u.msk = kNib;
-#pragma unroll
+        // kept rolled: one copy of the unit body keeps the hot code inside the instruction cache
+#pragma unroll 1
         for (int s = 0; s < UPT; ++s) {
             const int w = w0 + s;
             const int wn = w + 1 == p.Lw ? 0 : w + 1;
@@ -84,11 +90,11 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
     return delta;
 }
 
-template <int UPT>
-__global__ void __launch_bounds__(256) k_step_direct(const __grid_constant__ DirectParams p) {
+template <int UPT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, PGG_DIRECT_MIN_BLOCKS) k_step_direct(const __grid_constant__ DirectParams p) {
     __shared__ uint32_t s_table[kTableEntries];
     __shared__ int s_off;
-    __shared__ long long s_warp[8];
+    __shared__ long long s_warp[BLOCK / 32];
     for (int t = threadIdx.x; t < kTableEntries; t += blockDim.x) s_table[t] = p.table[t];
     if (threadIdx.x == 0) s_off = draw_offset(p.seed, p.k);
     __syncthreads();
@@ -114,18 +120,27 @@ __global__ void __launch_bounds__(256) k_step_direct(const __grid_constant__ Dir
     }
 }
 
-template <int UPT>
+template <int UPT, int BLOCK>
 int resident_grid() {
     static int grid = 0;  // per instance and process; the library drives one device type
     if (!grid) {
         int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_direct<UPT>, 256, 0) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_direct<UPT, BLOCK>, BLOCK, 0) != cudaSuccess)
             return 0;
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
+}
+
+template <int UPT, int BLOCK>
+cudaError_t launch_direct_instance(const DirectParams &p, cudaStream_t s) {
+    const int grid = resident_grid<UPT, BLOCK>();
+    if (!grid) return cudaErrorUnknown;
+    const int need = (p.n_tasks + BLOCK - 1) / BLOCK;
+    k_step_direct<UPT, BLOCK><<<need < grid ? need : grid, BLOCK, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -133,7 +148,7 @@ int resident_grid() {
 bool direct_supported(int layout, int L) { return layout == kPacked && L >= 256 && L % 256 == 0; }
 
 cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
-                               unsigned long long *running, int upt, cudaStream_t s) {
+                               unsigned long long *running, int upt, int block, cudaStream_t s) {
     if (L < 256 || L % 256 != 0 || (upt != 4 && upt != 8)) return cudaErrorInvalidValue;
     DirectParams p;
     p.lat = lat;
@@ -148,17 +163,10 @@ cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, 
     p.table = table;
     p.running = running;
     p.rk = philox_round_keys(seed);
-    const int need = (p.n_tasks + 255) / 256;
-    if (upt == 4) {
-        const int grid = resident_grid<4>();
-        if (!grid) return cudaErrorUnknown;
-        k_step_direct<4><<<need < grid ? need : grid, 256, 0, s>>>(p);
-    } else {
-        const int grid = resident_grid<8>();
-        if (!grid) return cudaErrorUnknown;
-        k_step_direct<8><<<need < grid ? need : grid, 256, 0, s>>>(p);
-    }
-    return cudaGetLastError();
+    // small blocks spread the step's few tasks evenly over the SMs
+    if (block == 128) return upt == 4 ? launch_direct_instance<4, 128>(p, s) : launch_direct_instance<8, 128>(p, s);
+    if (block == 256) return upt == 4 ? launch_direct_instance<4, 256>(p, s) : launch_direct_instance<8, 256>(p, s);
+    return upt == 4 ? launch_direct_instance<4, 64>(p, s) : launch_direct_instance<8, 64>(p, s);
 }
 
 }  // namespace pgg

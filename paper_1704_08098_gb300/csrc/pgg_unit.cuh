@@ -110,10 +110,10 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     const bool need0 = (active & 0x0000FFFFu) != 0, need1 = (active & 0xFFFF0000u) != 0;
     if (need0 && need1) {
         philox_rk2(u0, u1, rk);
-    } else if (need0) {
-        u0 = philox_rk(u0, rk);
     } else {
-        u1 = philox_rk(u1, rk);
+        // one call: a single inlined copy of the generator for either half
+        const uint4 r = philox_rk(need0 ? u0 : u1, rk);
+        if (need0) u0 = r; else u1 = r;
     }
 
     uint32_t flips = 0;

@@ -50,6 +50,8 @@ def _declare(lib):
         "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]),
         "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
+        "pgg_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _ip, _ip,
+                                        ctypes.POINTER(ctypes.c_float)]),
         "pgg_get_threshold_table": (ctypes.c_int, [_vp, _u32p]),
         "pgg_lattice_device_ptr": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), _u64p]),
         "pgg_step_mcs_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int,
@@ -203,6 +205,16 @@ class Lattice:
         names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto", KERNEL_DIRECT: "direct"}
         return dict(kernel=names[v[0].value], steps_per_launch=v[1].value, tile_x=v[2].value,
                     tile_y=v[3].value)
+
+    def autotune(self, n_mcs: int = 3) -> dict:
+        """pgg_autotune: pick the fastest schedule for this (device, L, layout)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        ms = ctypes.c_float()
+        check(self.lib.pgg_autotune(self._h, int(n_mcs), *[ctypes.byref(x) for x in v],
+                                    ctypes.byref(ms)), "pgg_autotune")
+        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_DIRECT: "direct"}
+        return dict(kernel=names[v[0].value], steps_per_launch=v[1].value, tile_x=v[2].value,
+                    tile_y=v[3].value, ms_per_mcs=float(ms.value))
 
     def threshold_table(self) -> np.ndarray:
         out = np.zeros(2 * 26 * 26, dtype=np.uint32)

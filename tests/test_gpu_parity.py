@@ -232,7 +232,8 @@ def test_full_size_against_oracle(o, pgg, L, n_mcs, layout):
     assert np.array_equal(got_lat, want_lat)
 
 
-DIRECT = {"direct4": dict(kernel="direct", tile_x=4), "direct8": dict(kernel="direct", tile_x=8)}
+DIRECT = {"direct4": dict(kernel="direct", tile_x=4, tile_y=128), "direct8": dict(kernel="direct", tile_x=8, tile_y=64),
+          "direct8b256": dict(kernel="direct", tile_x=8, tile_y=256)}
 
 
 @pytest.mark.parametrize("sched", sorted(DIRECT))
@@ -268,3 +269,22 @@ def test_direct_kernel_structured_and_switching(o, pgg):
     assert step == k
     assert np.array_equal(np.concatenate([c1, c2, c3]), np.concatenate(want))
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("layout,L", [("bitpack", 512), ("u8", 256), ("bitpack", 96)])
+def test_autotune_restores_state_and_keeps_results(o, pgg, layout, L):
+    """pgg_autotune times schedules on a saved copy and restores lattice, step and schedule;
+    the tuned AUTO schedule gives the same trajectory as the oracle."""
+    with pgg.Lattice(L, 3.85, 0.5, layout=layout) as lat:
+        lat.seed(5)
+        lat.step_mcs(2)
+        before, k_before = lat.get()
+        best = lat.autotune(1)
+        after, k_after = lat.get()
+        assert k_before == k_after and np.array_equal(before, after)
+        assert best["kernel"] in ("direct", "tiled", "simple") and best["ms_per_mcs"] > 0
+        counts = lat.step_mcs(6)
+        final, _ = lat.get()
+    ref = before.copy()
+    want = o.run(ref, 3.85, 0.5, 5, k_before, 6, threads=THREADS)
+    assert np.array_equal(counts, want) and np.array_equal(final, ref)
