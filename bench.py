@@ -37,7 +37,9 @@ FALLBACK_HBM_GBS = 6800.0
 # profiles/), keyed by the kernel's source file hash and launch configuration; they are used
 # only while that source is unchanged. alu_warp_inst = ALU-pipe warp instructions,
 # dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
-NCU = {}
+NCU = {
+    "direct:386f968aaf80d09d:bitpack:8192:1:4:64": {"alu_warp_inst": 4870544, "dram_bytes": 8450560},
+}
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
 ALU_LANES_PER_SM_CLOCK = 64
