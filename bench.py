@@ -148,6 +148,69 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClockSampler:
+    """SM clock and clock-event reasons polled every 2 ms through NVML (read-only calls),
+    for timed regions far shorter than nvidia-smi's sampling period."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device: int):
+        import ctypes
+        import torch
+        self.ok = False
+        self.samples = []
+        self.stop_flag = threading.Event()
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            pr = torch.cuda.get_device_properties(torch_device)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0".encode()
+            self.h = ctypes.c_void_p()
+            if self.nvml.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
+                return
+            v = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(v)) != 0:
+                return
+            self.max_mhz = float(v.value)
+            self.getr = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.ctypes = ctypes
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _run(self):
+        ct = self.ctypes
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0 and \
+                    self.getr(self.h, ct.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(0.002)
+
+    def start(self):
+        if self.ok:
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.thread.start()
+
+    def stop(self):
+        if not self.ok:
+            return None
+        self.stop_flag.set()
+        self.thread.join(timeout=2)
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml 2 ms"}
+
+
 def algorithmic_bytes_per_update(layout: str, k: int) -> float:
     """Bytes a launch of k fused sublattice steps must move per site update: it reads the
     whole lattice once and writes the N/16 updated sites (k = 1, in place) or the whole
@@ -253,7 +316,9 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
+    nvml = NvmlClockSampler(local)
     time.sleep(0.3)
+    nvml.start()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -268,7 +333,11 @@ def main():
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - wall0
+    fine = nvml.stop()
     clocks = sampler.stop()
+    if fine is not None:
+        fine["nvidia_smi"] = clocks
+        clocks = fine
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if world > 1:

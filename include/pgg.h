@@ -174,6 +174,56 @@ int pgg_step_mcs_noalloc(const void *lattice_in, void *lattice_out, int L, int l
                          double K, uint64_t seed, uint64_t step0, int64_t n_mcs,
                          uint64_t *coop_per_mcs, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched replicas: many independent lattices (each with its own L, r, K and seed) advanced
+ * by one persistent kernel launch. The paper simulates many lattice sizes and lengths near
+ * r_c (Section V); this runs such sets together. Every replica is bit-packed and kept in one
+ * SM's shared memory for the whole call, so L must be 64, 128, 256, 512 or 1024. A replica's
+ * trajectory is identical, bit for bit, to a pgg_ctx with the same (L, r, K, seed).
+ * --------------------------------------------------------------------------------------- */
+typedef struct pgg_batch pgg_batch;
+
+/* Create n replicas (arrays of length n, copied). Allocates their lattices and threshold
+ * tables on the current device; lattices start all-defector at step 0. */
+int pgg_batch_create(pgg_batch **out, int n, const int *L, const double *r, const double *K,
+                     const uint64_t *seeds, void *cuda_stream);
+
+/* Every replica: Bernoulli(p) initial state from its own seed (as pgg_seed); steps := 0. */
+int pgg_batch_seed(pgg_batch *b, double p);
+
+/* Advance every replica by n_mcs MCS in one launch. counts (nullable) receives n * n_mcs
+ * uint32 cooperator counts, replica-major ([i * n_mcs + m] = count of replica i after MCS m),
+ * in device memory (asynchronous) or host memory (the call synchronises). */
+int pgg_batch_step_mcs(pgg_batch *b, int n_mcs, uint32_t *counts);
+
+/* Warps that advance one replica, per size class L = 64, 128, 256, 512, 1024 (5 entries,
+ * each 1, 2, 4, 8, 16 or 32). Default {1, 1, 2, 8, 32}. Results do not depend on it. */
+int pgg_batch_set_team_warps(pgg_batch *b, const int *warps);
+int pgg_batch_get_team_warps(const pgg_batch *b, int *warps);
+
+/* Threads per persistent CTA: 1024 (default) or 512 (fewer warps, more registers each). */
+int pgg_batch_set_cta_threads(pgg_batch *b, int threads);
+int pgg_batch_get_cta_threads(const pgg_batch *b, int *threads);
+
+/* Autotuner: time candidate (CTA size, team sizes) for n_mcs MCS on a saved copy of the
+ * replicas, restore them, keep the fastest; warps_out (nullable, 5 entries) and ms_out
+ * (nullable) receive the choice and its time for the n_mcs MCS. Synchronises the stream. */
+int pgg_batch_autotune(pgg_batch *b, int n_mcs, int *warps_out, float *ms_out);
+
+/* pgg_batch_step_mcs captures its persistent launch in a CUDA graph (once per n_mcs) and
+ * replays it (enable = 1, default), or launches directly (enable = 0). */
+int pgg_batch_use_graph(pgg_batch *b, int enable);
+
+/* Replica i's lattice (L*L bytes, 1 = C) and step counter, or replace them. Synchronise. */
+int pgg_batch_get_lattice(pgg_batch *b, int i, uint8_t *host_out, uint64_t *step_out);
+int pgg_batch_set_lattice(pgg_batch *b, int i, const uint8_t *host_in, uint64_t step);
+
+/* Number of replicas. */
+int pgg_batch_size(const pgg_batch *b, int *n);
+
+/* Release the batch (NULL accepted). Synchronises the stream. */
+void pgg_batch_destroy(pgg_batch *b);
+
 /* Release the context and its device memory. NULL is accepted. Synchronises the stream. */
 void pgg_destroy(pgg_ctx *ctx);
 

@@ -58,6 +58,21 @@ def _declare(lib):
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                                 ctypes.c_uint64, ctypes.c_int64, _vp, _vp]),
         "pgg_destroy": (None, [_vp]),
+        "pgg_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _ip,
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), _u64p, _vp]),
+        "pgg_batch_seed": (ctypes.c_int, [_vp, ctypes.c_double]),
+        "pgg_batch_step_mcs": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+        "pgg_batch_set_team_warps": (ctypes.c_int, [_vp, _ip]),
+        "pgg_batch_get_team_warps": (ctypes.c_int, [_vp, _ip]),
+        "pgg_batch_set_cta_threads": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "pgg_batch_get_cta_threads": (ctypes.c_int, [_vp, _ip]),
+        "pgg_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _ip, ctypes.POINTER(ctypes.c_float)]),
+        "pgg_batch_use_graph": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "pgg_batch_get_lattice": (ctypes.c_int, [_vp, ctypes.c_int, _u8p, _u64p]),
+        "pgg_batch_set_lattice": (ctypes.c_int, [_vp, ctypes.c_int, _u8p, ctypes.c_uint64]),
+        "pgg_batch_size": (ctypes.c_int, [_vp, _ip]),
+        "pgg_batch_destroy": (None, [_vp]),
         "pgg_last_error": (ctypes.c_char_p, []),
         "pgg_version": (ctypes.c_char_p, []),
     }
@@ -240,6 +255,103 @@ def step_mcs_noalloc(lattice_in: int, lattice_out: int, L: int, layout, r: float
                                    LAYOUTS[layout], float(r), float(K), int(seed), int(step0),
                                    int(n_mcs), _vp(int(counts_dev)) if counts_dev else None,
                                    _vp(st)), "pgg_step_mcs_noalloc")
+
+
+class Batch:
+    """Many replicas advanced in one persistent launch (``pgg_batch``)."""
+
+    def __init__(self, L, r, K, seeds, stream: int | None = None):
+        self.lib = load()
+        self.L = np.ascontiguousarray(L, dtype=np.int32)
+        n = self.L.size
+        rr = np.ascontiguousarray(np.broadcast_to(np.asarray(r, dtype=np.float64), (n,)))
+        KK = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.float64), (n,)))
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        assert rr.size == n and KK.size == n and sd.size == n
+        self.n = n
+        self.stream = current_stream_handle() if stream is None else int(stream)
+        h = _vp()
+        check(self.lib.pgg_batch_create(ctypes.byref(h), n, _ptr(self.L, _ip),
+                                        _ptr(rr, ctypes.POINTER(ctypes.c_double)),
+                                        _ptr(KK, ctypes.POINTER(ctypes.c_double)),
+                                        _ptr(sd, _u64p), _vp(self.stream)), "pgg_batch_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.pgg_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seed(self, p: float = 0.5) -> None:
+        check(self.lib.pgg_batch_seed(self._h, float(p)), "pgg_batch_seed")
+
+    def step_mcs(self, n_mcs: int, counts=True):
+        """Advance all replicas; counts=True returns an (n, n_mcs) uint32 host array,
+        counts=None skips them, an int is a device pointer filled asynchronously."""
+        if counts is None or counts is False:
+            check(self.lib.pgg_batch_step_mcs(self._h, int(n_mcs), None), "pgg_batch_step_mcs")
+            return None
+        if counts is True:
+            out = np.zeros((self.n, max(int(n_mcs), 1)), dtype=np.uint32)
+            check(self.lib.pgg_batch_step_mcs(self._h, int(n_mcs), out.ctypes.data),
+                  "pgg_batch_step_mcs")
+            return out[:, :n_mcs]
+        check(self.lib.pgg_batch_step_mcs(self._h, int(n_mcs), _vp(int(counts))),
+              "pgg_batch_step_mcs")
+        return None
+
+    def get(self, i: int) -> tuple[np.ndarray, int]:
+        L = int(self.L[i])
+        out = np.empty((L, L), dtype=np.uint8)
+        step = ctypes.c_uint64()
+        check(self.lib.pgg_batch_get_lattice(self._h, int(i), _ptr(out, _u8p), ctypes.byref(step)),
+              "pgg_batch_get_lattice")
+        return out, int(step.value)
+
+    def set(self, i: int, lattice: np.ndarray, step: int = 0) -> None:
+        a = np.ascontiguousarray(lattice, dtype=np.uint8)
+        check(self.lib.pgg_batch_set_lattice(self._h, int(i), _ptr(a, _u8p), int(step)),
+              "pgg_batch_set_lattice")
+
+    def set_team_warps(self, warps) -> None:
+        w = np.ascontiguousarray(warps, dtype=np.int32)
+        check(self.lib.pgg_batch_set_team_warps(self._h, _ptr(w, _ip)), "pgg_batch_set_team_warps")
+
+    def team_warps(self) -> list[int]:
+        w = np.zeros(5, dtype=np.int32)
+        check(self.lib.pgg_batch_get_team_warps(self._h, _ptr(w, _ip)), "pgg_batch_get_team_warps")
+        return [int(x) for x in w]
+
+    def set_cta_threads(self, threads: int) -> None:
+        check(self.lib.pgg_batch_set_cta_threads(self._h, int(threads)), "pgg_batch_set_cta_threads")
+
+    def cta_threads(self) -> int:
+        v = ctypes.c_int()
+        check(self.lib.pgg_batch_get_cta_threads(self._h, ctypes.byref(v)), "pgg_batch_get_cta_threads")
+        return int(v.value)
+
+    def use_graph(self, enable: bool) -> None:
+        check(self.lib.pgg_batch_use_graph(self._h, int(bool(enable))), "pgg_batch_use_graph")
+
+    def autotune(self, n_mcs: int = 20) -> dict:
+        w = np.zeros(5, dtype=np.int32)
+        ms = ctypes.c_float()
+        check(self.lib.pgg_batch_autotune(self._h, int(n_mcs), _ptr(w, _ip), ctypes.byref(ms)),
+              "pgg_batch_autotune")
+        return dict(team_warps=[int(x) for x in w], cta_threads=self.cta_threads(),
+                    ms=float(ms.value))
 
 
 def version() -> str:
