@@ -224,6 +224,46 @@ int pgg_batch_size(const pgg_batch *b, int *n);
 /* Release the batch (NULL accepted). Synchronises the stream. */
 void pgg_batch_destroy(pgg_batch *b);
 
+/* ---------------------------------------------------------------------------------------
+ * Surrogate network for the r_c search. The paper locates r_c from long runs (Section V,
+ * Fig. 4); this small network reads the first 200 samples of rho_C(t) of a run plus its
+ * normalised (r, K) and predicts P(absorbing) and the stationary rho_C, so that a bisection
+ * can stop replicas early. 202 -> 128 (relu) -> 128 (relu) -> 2 (sigmoid heads); BF16
+ * parameters rounded to nearest even from an FP32 master copy, FP32 accumulation; Adam
+ * (beta 0.9 / 0.999, eps 1e-8, bias corrected). Parameters are packed W1 (128x202 row-major),
+ * b1, W2 (128x128), b2, W3 (2x128), b3. X (B x 202), Y (B x 3: absorbed 0/1, stationary
+ * rho, mask of the rho term) and outputs are row-major FP32 device buffers.
+ * Loss = mean BCE(p, absorbed) + mean(mask * (rho - y_rho)^2).
+ * --------------------------------------------------------------------------------------- */
+typedef struct pgg_mlp pgg_mlp;
+
+/* Layer sizes and parameter count (any pointer may be NULL). */
+int pgg_mlp_info(int *n_in, int *n_hidden, int *n_out, int *n_params);
+
+/* Network for batches of up to max_batch rows; parameters start at zero. */
+int pgg_mlp_create(pgg_mlp **out, int max_batch, void *cuda_stream);
+
+/* Load the FP32 master parameters from host memory (n_params floats); resets Adam. */
+int pgg_mlp_set_params(pgg_mlp *n, const float *host_master);
+
+/* Copy the FP32 master parameters and/or their BF16 image (raw uint16) to host memory. */
+int pgg_mlp_get_params(pgg_mlp *n, float *host_master, uint16_t *host_bf16);
+
+/* out[b] = (P(absorbing), stationary rho) for the B rows of X. Asynchronous. */
+int pgg_mlp_forward(pgg_mlp *n, const float *X, int B, float *out);
+
+/* Loss (1 float, nullable) and gradient (n_params floats, nullable) into device memory. */
+int pgg_mlp_loss_grad(pgg_mlp *n, const float *X, const float *Y, int B, float *loss_out,
+                      float *grad_out);
+
+/* One Adam step with learning rate lr on the batch; loss of the batch before the step into
+ * loss_out (device, nullable). Asynchronous. */
+int pgg_mlp_train_step(pgg_mlp *n, const float *X, const float *Y, int B, float lr,
+                       float *loss_out);
+
+/* Release the network (NULL accepted). */
+void pgg_mlp_destroy(pgg_mlp *n);
+
 /* Release the context and its device memory. NULL is accepted. Synchronises the stream. */
 void pgg_destroy(pgg_ctx *ctx);
 

@@ -41,6 +41,34 @@ def replica_sizes(n: int, choices, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).choice(np.asarray(choices), size=n)
 
 
+def mlp_init_params(seed: int, n_in: int = 202, n_hidden: int = 128, n_out: int = 2) -> np.ndarray:
+    """Initial surrogate parameters (float32, packed W1, b1, W2, b2, W3, b3): weights uniform
+    in +-sqrt(6 / fan_in) (He-uniform), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((n_hidden, n_in), (n_hidden, n_hidden), (n_out, n_hidden)):
+        lim = np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def random_features(B: int, seed: int, n_in: int = 202) -> np.ndarray:
+    """B random surrogate inputs: 200 cooperator fractions in [0, 1] then normalised r, K."""
+    rng = np.random.default_rng(seed)
+    X = rng.random((B, n_in)).astype(np.float32)
+    X[:, -2:] = rng.uniform(-1, 1, size=(B, 2)).astype(np.float32)
+    return X
+
+
+def random_labels(B: int, seed: int) -> np.ndarray:
+    """B random (absorbed, stationary rho, mask) label rows."""
+    rng = np.random.default_rng(seed)
+    y = (rng.random(B) < 0.5).astype(np.float32)
+    rho = np.where(y > 0, 0.0, rng.random(B)).astype(np.float32)
+    return np.stack([y, rho, 1.0 - y], axis=1).astype(np.float32)
+
+
 # Workloads used by the tests and the benchmark (sizes and parameters of
 # the paper's experiments: Section V, Fig. 4 and Fig. 5).
 WORKLOADS = {

@@ -73,6 +73,15 @@ def _declare(lib):
         "pgg_batch_set_lattice": (ctypes.c_int, [_vp, ctypes.c_int, _u8p, ctypes.c_uint64]),
         "pgg_batch_size": (ctypes.c_int, [_vp, _ip]),
         "pgg_batch_destroy": (None, [_vp]),
+        "pgg_mlp_info": (ctypes.c_int, [_ip, _ip, _ip, _ip]),
+        "pgg_mlp_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+        "pgg_mlp_set_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+        "pgg_mlp_get_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(ctypes.c_uint16)]),
+        "pgg_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+        "pgg_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
+        "pgg_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp]),
+        "pgg_mlp_destroy": (None, [_vp]),
         "pgg_last_error": (ctypes.c_char_p, []),
         "pgg_version": (ctypes.c_char_p, []),
     }
@@ -352,6 +361,67 @@ class Batch:
               "pgg_batch_autotune")
         return dict(team_warps=[int(x) for x in w], cta_threads=self.cta_threads(),
                     ms=float(ms.value))
+
+
+class MLP:
+    """The surrogate network (``pgg_mlp``); X, Y and outputs are device pointers (int)."""
+
+    def __init__(self, max_batch: int, stream: int | None = None):
+        self.lib = load()
+        v = [ctypes.c_int() for _ in range(4)]
+        check(self.lib.pgg_mlp_info(*[ctypes.byref(x) for x in v]), "pgg_mlp_info")
+        self.n_in, self.n_hidden, self.n_out, self.n_params = (x.value for x in v)
+        self.max_batch = int(max_batch)
+        self.stream = current_stream_handle() if stream is None else int(stream)
+        h = _vp()
+        check(self.lib.pgg_mlp_create(ctypes.byref(h), self.max_batch, _vp(self.stream)),
+              "pgg_mlp_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.pgg_mlp_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, master: np.ndarray) -> None:
+        a = np.ascontiguousarray(master, dtype=np.float32)
+        assert a.size == self.n_params
+        check(self.lib.pgg_mlp_set_params(self._h, _ptr(a, ctypes.POINTER(ctypes.c_float))),
+              "pgg_mlp_set_params")
+
+    def get_params(self) -> tuple[np.ndarray, np.ndarray]:
+        """(FP32 master, BF16 image as float32 values)."""
+        m = np.zeros(self.n_params, dtype=np.float32)
+        q = np.zeros(self.n_params, dtype=np.uint16)
+        check(self.lib.pgg_mlp_get_params(self._h, _ptr(m, ctypes.POINTER(ctypes.c_float)),
+                                          _ptr(q, ctypes.POINTER(ctypes.c_uint16))),
+              "pgg_mlp_get_params")
+        return m, (q.astype(np.uint32) << 16).view(np.float32)
+
+    def forward(self, X_dev: int, B: int, out_dev: int) -> None:
+        check(self.lib.pgg_mlp_forward(self._h, _vp(X_dev), int(B), _vp(out_dev)), "pgg_mlp_forward")
+
+    def loss_grad(self, X_dev: int, Y_dev: int, B: int, loss_dev: int | None,
+                  grad_dev: int | None) -> None:
+        check(self.lib.pgg_mlp_loss_grad(self._h, _vp(X_dev), _vp(Y_dev), int(B),
+                                         _vp(loss_dev) if loss_dev else None,
+                                         _vp(grad_dev) if grad_dev else None), "pgg_mlp_loss_grad")
+
+    def train_step(self, X_dev: int, Y_dev: int, B: int, lr: float, loss_dev: int | None = None) -> None:
+        check(self.lib.pgg_mlp_train_step(self._h, _vp(X_dev), _vp(Y_dev), int(B), float(lr),
+                                          _vp(loss_dev) if loss_dev else None), "pgg_mlp_train_step")
 
 
 def version() -> str:
