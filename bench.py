@@ -211,6 +211,23 @@ class NvmlClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml 2 ms"}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Maximum of x over all ranks (the slowest rank sets the job's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(sites_per_step: float, steps: int, world: int, max_total_ms: float) -> float:
+    """Whole-job site updates per second: every rank advances its own lattice."""
+    return sites_per_step * steps * world / (max_total_ms / 1e3)
+
+
 def algorithmic_bytes_per_update(layout: str, k: int) -> float:
     """Bytes a launch of k fused sublattice steps must move per site update: it reads the
     whole lattice once and writes the N/16 updated sites (k = 1, in place) or the whole
@@ -286,6 +303,7 @@ def main():
         run_reference(args, rank, world)
         if world > 1:
             import torch.distributed as dist
+            dist.barrier()
             dist.destroy_process_group()
         return
 
@@ -339,13 +357,8 @@ def main():
         fine["nvidia_smi"] = clocks
         clocks = fine
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    updates = float(L) * L * args.steps * world
-    value = updates / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = job_value(float(L) * L, args.steps, world, total_ms)
 
     # dominant kernel: the step kernel, 16 / k launches per MCS; its launch duration is the
     # MCS time / launches (includes launch gaps, so it understates the kernel's own rate)
