@@ -78,11 +78,17 @@ typedef enum {
     PGG_KERNEL_TILED = 2,  /* shared-memory tiles with a 3k-site halo, k sublattice
                               steps fused per launch (temporal blocking); k = 1 runs in
                               place, k > 1 ping-pongs between two lattice buffers */
-    PGG_KERNEL_DIRECT = 3  /* bit-packed lattices with L % 256 == 0 only: one launch per
+    PGG_KERNEL_DIRECT = 3, /* bit-packed lattices with L % 256 == 0 only: one launch per
                               sublattice step, in place, operands straight from global
                               memory, tile_x = words per thread (4 or 8), tile_y = threads
                               per block (64, 128 or 256); the cooperator count is carried as
                               a running total */
+    PGG_KERNEL_RESIDENT = 4 /* bit-packed lattices with L % 256 == 0 whose rows fit the SMs'
+                              shared memory: one cooperative launch per pgg_step_mcs call,
+                              each CTA keeps a band of rows for all MCS and exchanges its 3
+                              edge rows with its neighbours between sublattice steps; waits
+                              are bounded (a time-out returns PGG_ERR_TIMEOUT at the next
+                              synchronising call) */
 } pgg_kernel;
 
 /* Create a context for one L x L lattice with synergy factor r and noise K (Section III,
@@ -139,6 +145,11 @@ int pgg_set_schedule(pgg_ctx *ctx, int kernel, int steps_per_launch, int tile_x,
  * one lattice-sized temporary. Results do not depend on the schedule. */
 int pgg_autotune(pgg_ctx *ctx, int n_mcs, int *kernel, int *steps_per_launch, int *tile_x,
                  int *tile_y, float *ms_per_mcs);
+
+/* Polls a CTA of PGG_KERNEL_RESIDENT makes on a neighbour's step counter before it gives up
+ * and flags a time-out (default 1 << 22, about a second). 0 makes every wait fail at once,
+ * for testing the failure path. */
+int pgg_set_spin_limit(pgg_ctx *ctx, unsigned int limit);
 
 /* The schedule pgg_step_mcs will use (after AUTO resolution). Any pointer may be NULL. */
 int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int *tile_x,

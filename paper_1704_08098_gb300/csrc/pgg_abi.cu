@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -98,6 +99,13 @@ struct pgg_ctx {
     int tile_x = 0, tile_y = 0;
     unsigned long long *running_d = nullptr;  // cooperator count carried by the direct kernel
     bool running_valid = false;               // running_d equals the lattice's count
+    // resident kernel
+    int sms = 0;
+    size_t smem_optin = 0;
+    uint32_t *mailbox_d = nullptr;
+    unsigned int *ctr_d = nullptr;
+    int *status_d = nullptr;
+    unsigned int spin_limit = 1u << 22;
 };
 
 namespace {
@@ -135,6 +143,12 @@ Schedule resolve_schedule(const pgg_ctx *c) {
             s.tile_x = 0;
             s.tile_y = 0;
         }
+    }
+    if (s.kernel == PGG_KERNEL_RESIDENT) {
+        s.k = 16;
+        s.tile_x = pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin);
+        s.tile_y = 0;
+        return s;
     }
     if (s.kernel == PGG_KERNEL_DIRECT) {
         s.k = 1;
@@ -181,6 +195,23 @@ int ensure_staging(pgg_ctx *c) {
     return PGG_OK;
 }
 
+// Report (and clear) a bounded wait that ran out in an earlier resident launch.
+int check_status(pgg_ctx *c) {
+    int st = 0;
+    PGG_CUDA(cudaMemcpyAsync(&st, c->status_d, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    if (st) {
+        PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
+        PGG_CUDA(cudaStreamSynchronize(c->stream));
+        c->running_valid = false;
+        return fail(PGG_ERR_TIMEOUT,
+                    "a resident-kernel CTA waited longer than %u polls for a neighbour; the lattice is not "
+                    "a valid state (restore it with pgg_set_lattice or pgg_seed)",
+                    c->spin_limit);
+    }
+    return PGG_OK;
+}
+
 bool is_device_pointer(const void *p) {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
@@ -221,16 +252,26 @@ int pgg_create(pgg_ctx **out, int L, double r, double K, int layout, void *cuda_
         delete c;
         return fail(PGG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     }
+    {
+        int sms = 0, optin = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) == cudaSuccess) {
+            c->sms = sms;
+            c->smem_optin = static_cast<size_t>(optin) > 2048 ? static_cast<size_t>(optin) - 2048 : 0;
+        }
+    }
     const uint64_t sites = static_cast<uint64_t>(L) * L;
     c->lat_bytes = layout == PGG_U8 ? sites : sites / 8;
     pgg::build_threshold_table(r, K, c->table_h);
     if ((e = cudaMalloc(&c->lat, c->lat_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&c->table_d, sizeof c->table_h)) != cudaSuccess) {
+        (e = cudaMalloc(&c->table_d, sizeof c->table_h)) != cudaSuccess ||
+        (e = cudaMalloc(&c->status_d, sizeof(int))) != cudaSuccess) {
         pgg_destroy(c);
         return fail(PGG_ERR_OOM, "pgg_create: cudaMalloc: %s", cudaGetErrorString(e));
     }
     if ((e = cudaMemcpyAsync(c->table_d, c->table_h, sizeof c->table_h, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->lat, 0, c->lat_bytes, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
         pgg_destroy(c);
         return fail(PGG_ERR_CUDA, "pgg_create: %s", cudaGetErrorString(e));
@@ -280,6 +321,47 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     const Schedule s = resolve_schedule(c);
     if (s.kernel == PGG_KERNEL_TILED && s.k > 1 && (rc = ensure_alt(c))) return rc;
     PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, static_cast<size_t>(n_mcs) * sizeof(unsigned long long), c->stream));
+    if (s.kernel == PGG_KERNEL_RESIDENT) {
+        const int bands = s.tile_x;
+        if (bands < 1) return fail(PGG_ERR_STATE, "pgg_step_mcs: the lattice cannot be resident");
+        if (!c->mailbox_d) {
+            cudaError_t e = cudaMalloc(&c->mailbox_d, pgg::resident_mailbox_words(c->L, bands) * sizeof(uint32_t));
+            if (e == cudaSuccess) e = cudaMalloc(&c->ctr_d, sizeof(unsigned int) * bands);
+            if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(resident buffers): %s", cudaGetErrorString(e));
+        }
+        pgg::ResidentArgs a;
+        a.lat = static_cast<uint32_t *>(c->lat);
+        a.L = c->L;
+        a.n_bands = bands;
+        a.seed = c->seed;
+        a.k0 = c->step;
+        a.table = c->table_d;
+        a.mailbox = c->mailbox_d;
+        a.ctr = c->ctr_d;
+        a.status = c->status_d;
+        a.spin_limit = c->spin_limit;
+        // one launch covers at most 1 << 16 MCS
+        for (int64_t m0 = 0; m0 < n_mcs; m0 += (1 << 16)) {
+            a.n_mcs = static_cast<int>(std::min<int64_t>(n_mcs - m0, 1 << 16));
+            a.counts = c->counts_d + m0;
+            a.k0 = c->step;
+            PGG_CUDA(pgg::launch_resident(a, c->stream));
+            c->step += 16ull * static_cast<uint64_t>(a.n_mcs);
+        }
+        c->running_valid = false;
+        if (coop_per_mcs) {
+            const size_t bytes = static_cast<size_t>(n_mcs) * sizeof(uint64_t);
+            if (is_device_pointer(coop_per_mcs)) {
+                PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            } else {
+                PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToHost, c->stream));
+                PGG_CUDA(cudaStreamSynchronize(c->stream));
+                return check_status(c);
+            }
+        }
+        PGG_CUDA(cudaGetLastError());
+        return PGG_OK;
+    }
     if (s.kernel == PGG_KERNEL_DIRECT) {
         if (!c->running_d) {
             cudaError_t e = cudaMalloc(&c->running_d, sizeof(unsigned long long));
@@ -358,7 +440,7 @@ int pgg_count_coop(pgg_ctx *c, uint64_t *out) {
     PGG_CUDA(cudaMemcpyAsync(&v, c->counts_d, sizeof v, cudaMemcpyDeviceToHost, c->stream));
     PGG_CUDA(cudaStreamSynchronize(c->stream));
     *out = v;
-    return PGG_OK;
+    return check_status(c);
 }
 
 int pgg_get_lattice(pgg_ctx *c, uint8_t *host_out, uint64_t *step_out) {
@@ -376,7 +458,7 @@ int pgg_get_lattice(pgg_ctx *c, uint8_t *host_out, uint64_t *step_out) {
     }
     PGG_CUDA(cudaStreamSynchronize(c->stream));
     if (step_out) *step_out = c->step;
-    return PGG_OK;
+    return check_status(c);
 }
 
 int pgg_set_lattice(pgg_ctx *c, const uint8_t *host_in, uint64_t step) {
@@ -412,8 +494,17 @@ int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, i
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_set_schedule: NULL context");
     if (kernel != PGG_KERNEL_AUTO && kernel != PGG_KERNEL_SIMPLE && kernel != PGG_KERNEL_TILED &&
-        kernel != PGG_KERNEL_DIRECT)
+        kernel != PGG_KERNEL_DIRECT && kernel != PGG_KERNEL_RESIDENT)
         return fail(PGG_ERR_ARG, "pgg_set_schedule: unknown kernel %d", kernel);
+    if (kernel == PGG_KERNEL_RESIDENT) {
+        if (pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) < 1)
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: this lattice cannot be resident (bit-packed, L %% 256 == 0, rows within shared memory)");
+        c->kernel = kernel;
+        c->k_fuse = 16;
+        c->tile_x = 0;
+        c->tile_y = 0;
+        return PGG_OK;
+    }
     if (kernel == PGG_KERNEL_DIRECT) {
         if (!pgg::direct_supported(c->layout, c->L))
             return fail(PGG_ERR_ARG, "pgg_set_schedule: the direct kernel needs a bit-packed lattice with L %% 256 == 0");
@@ -442,6 +533,13 @@ int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, i
     c->k_fuse = kernel == PGG_KERNEL_TILED ? steps_per_launch : 1;
     c->tile_x = kernel == PGG_KERNEL_TILED ? tile_x : 0;
     c->tile_y = kernel == PGG_KERNEL_TILED ? tile_y : 0;
+    return PGG_OK;
+}
+
+int pgg_set_spin_limit(pgg_ctx *c, unsigned int limit) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_set_spin_limit: NULL context");
+    c->spin_limit = limit;
     return PGG_OK;
 }
 
@@ -479,6 +577,7 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
     PGG_CUDA(cudaSetDevice(c->device));
     // candidates
     std::vector<Schedule> cand;
+    if (pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) > 0) cand.push_back({PGG_KERNEL_RESIDENT, 16, 0, 0});
     if (pgg::direct_supported(c->layout, c->L))
         for (int upt : {4, 8})
             for (int blk : {64, 128, 256}) cand.push_back({PGG_KERNEL_DIRECT, 1, upt, blk});
@@ -570,6 +669,9 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->counts_d) cudaFree(c->counts_d);
     if (c->staging_d) cudaFree(c->staging_d);
     if (c->running_d) cudaFree(c->running_d);
+    if (c->mailbox_d) cudaFree(c->mailbox_d);
+    if (c->ctr_d) cudaFree(c->ctr_d);
+    if (c->status_d) cudaFree(c->status_d);
     delete c;
 }
 

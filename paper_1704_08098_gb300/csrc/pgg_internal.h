@@ -66,4 +66,23 @@ cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, 
 // Shared memory (bytes) the tiled kernel needs for a configuration; 0 if unsupported.
 size_t tiled_smem_bytes(int layout, int steps, int tile_x, int tile_y);
 
+// Whole bit-packed lattice resident in shared memory for n_mcs MCS (one cooperative launch,
+// one row band per CTA, edge rows exchanged through a mailbox between steps).
+struct ResidentArgs {
+    uint32_t *lat;
+    int L;
+    int n_bands;
+    uint64_t seed, k0;
+    int n_mcs;
+    const uint32_t *table;
+    uint32_t *mailbox;            // resident_mailbox_words(L, n_bands) words
+    unsigned int *ctr;            // n_bands counters
+    unsigned long long *counts;   // n_mcs counts, zeroed by the caller
+    int *status;                  // set to 1 if a bounded wait ran out
+    unsigned int spin_limit;      // polls before a wait gives up
+};
+int resident_bands(int layout, int L, int sms, size_t smem_optin);
+size_t resident_mailbox_words(int L, int n_bands);
+cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s);
+
 }  // namespace pgg

@@ -1,0 +1,247 @@
+// pgg_kernels_resident.cu -- a whole bit-packed lattice resident in shared memory across
+// many MCS: one cooperative launch, each CTA owning a band of rows.
+//
+// CTA b keeps rows [r0, r1) of the lattice plus 3 halo rows above and below in shared memory
+// for the whole call. A sublattice step writes only rows i = oi (mod 4), at least 4 apart, and
+// an update reads rows i-3 .. i+3 (Section IV, Fig. 3), so within a step no CTA needs data a
+// neighbour writes in that step; between steps each CTA publishes its 3 top and 3 bottom band
+// rows to a double-buffered mailbox in global memory, bumps its step counter, and before the
+// next step waits for both neighbours' counters and copies their edge rows into its halo.
+// All CTAs are co-resident (cooperative launch). Every wait is bounded: after `spin_limit`
+// polls the CTA sets the status word and stops; its neighbours then time out in turn.
+//
+// Per step the work is the direct kernel's: tasks of one sublattice row and 8 words (one
+// direction call), the shared update core of pgg_unit.cuh, in place in shared memory. The
+// count after each MCS is the sum of the bands' population counts.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "pgg_device.cuh"
+#include "pgg_internal.h"
+#include "pgg_unit.cuh"
+
+namespace pgg {
+namespace {
+
+constexpr int kResThreads = 512;
+constexpr int kResUPT = 8;  // words per task: one direction call
+
+struct ResidentParams {
+    uint32_t *lat;            // global lattice (read at the start, written at the end)
+    int L, Lw, n_bands;
+    uint64_t seed, k0;
+    int n_mcs;
+    const uint32_t *table;
+    uint32_t *mailbox;        // [band][parity][top/bottom][3 rows][Lw]
+    unsigned int *ctr;        // [band] completed steps
+    unsigned long long *counts;  // [n_mcs], zeroed before the launch
+    int *status;              // set to 1 on a wait time-out
+    unsigned int spin_limit;
+    PhiloxKeys rk;
+};
+
+__device__ __forceinline__ int band_start(int b, int L, int n) { return static_cast<int>((static_cast<long long>(b) * L) / n); }
+
+// Word w of a band row lives at (w ^ ((w >> 5) & 7)): the 32 lanes of a warp, which start
+// tasks 8 words apart, then hit 32 different banks.
+__device__ __forceinline__ int swz(int w) { return w ^ ((w >> 5) & 7); }
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int OJ>
+__device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *__restrict__ s_table,
+                                              const PhiloxKeys &rk, int L, int Lw, int r0, int nb,
+                                              uint64_t k, int oi) {
+    // sublattice rows of the band: global rows r in [r0, r0 + nb) with r = oi (mod 4)
+    const int first = r0 + ((oi - r0) & 3);
+    const int n_srows = first < r0 + nb ? (r0 + nb - first + 3) >> 2 : 0;
+    const int runs = Lw / kResUPT;
+    const int n_tasks = n_srows * runs;
+    const uint32_t kl = static_cast<uint32_t>(k), kh = static_cast<uint32_t>(k >> 32) | kTagDir;
+    for (int t = threadIdx.x; t < n_tasks; t += kResThreads) {
+        const int sr = t / runs;  // runs is a power of two only for power-of-two L; keep exact
+        const int c = t - sr * runs;
+        const int i = first + 4 * sr;            // global row
+        const int lr = i - r0 + 3;               // local row (3 halo rows above the band)
+        const uint32_t *row0 = s_rows + (lr - 3) * Lw;
+        const int w0 = kResUPT * c;
+        const int wprev = w0 == 0 ? Lw - 1 : w0 - 1;
+        uint32_t wl[7], wc[7], wr[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            wl[q] = row0[q * Lw + swz(wprev)];
+            wc[q] = row0[q * Lw + swz(w0)];
+        }
+        const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(c), static_cast<uint32_t>(i >> 2), kl, kh), rk);
+        UnitCtx u;
+        u.k = k;
+        u.a = static_cast<uint32_t>(i >> 2);
+        u.msk = kNib;
+#pragma unroll 1
+        for (int w = w0; w < w0 + kResUPT; ++w) {
+            const int wn = w + 1 == Lw ? 0 : w + 1;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) wr[q] = row0[q * Lw + swz(wn)];
+            u.gw = w;
+            u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
+            uint32_t sx;
+            const uint32_t flips = unit_flips<OJ>(wl, wc, wr, u, rk, s_table, sx);
+            if (flips) s_rows[lr * Lw + swz(w)] = wc[3] ^ (flips << OJ);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                wl[q] = wc[q];
+                wc[q] = wr[q];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_constant__ ResidentParams p) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *s_table = smem;
+    uint32_t *s_rows = smem + kTableEntries;
+    __shared__ int s_abort;
+    __shared__ unsigned long long s_warp[kResThreads / 32];
+    const int b = blockIdx.x, nbnd = p.n_bands;
+    const int L = p.L, Lw = p.Lw;
+    const int r0 = band_start(b, L, nbnd), nb = band_start(b + 1, L, nbnd) - r0;
+    const int up = (b + nbnd - 1) % nbnd, down = (b + 1) % nbnd;
+    const size_t edge = static_cast<size_t>(3) * Lw;  // words of 3 rows
+    const PhiloxKeys rk = p.rk;
+    for (int t = threadIdx.x; t < kTableEntries; t += kResThreads) s_table[t] = p.table[t];
+    if (threadIdx.x == 0) s_abort = 0;
+    // stage band + halo (rows r0 - 3 .. r0 + nb + 2, periodic)
+    for (int x = threadIdx.x; x < (nb + 6) * Lw; x += kResThreads) {
+        const int lr = x / Lw, w = x - lr * Lw;
+        const int g = wrap_small(r0 - 3 + lr, L);
+        s_rows[lr * Lw + swz(w)] = p.lat[static_cast<size_t>(g) * Lw + w];
+    }
+    __syncthreads();
+    uint4 ocall = make_uint4(0, 0, 0, 0);
+    uint64_t ocall_idx = ~0ull;
+    const int total = 16 * p.n_mcs;
+    for (int j = 0; j < total; ++j) {
+        const uint64_t k = p.k0 + static_cast<uint64_t>(j);
+        if (j > 0) {
+            // neighbours finished step j - 1 and published their edge rows
+            if (threadIdx.x == 0) {
+                unsigned int it = 0;
+                while ((load_acquire(&p.ctr[up]) < static_cast<unsigned int>(j) ||
+                        load_acquire(&p.ctr[down]) < static_cast<unsigned int>(j)) && it < p.spin_limit) {
+                    __nanosleep(64);
+                    ++it;
+                }
+                if (it >= p.spin_limit) {
+                    atomicExch(p.status, 1);
+                    s_abort = 1;
+                }
+            }
+            __syncthreads();
+            if (s_abort) return;  // no copies in flight; the lattice in global memory is left as it was
+            const int par = (j - 1) & 1;
+            const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * edge;   // its bottom rows
+            const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * edge; // its top rows
+            for (int x = threadIdx.x; x < 3 * Lw; x += kResThreads) {
+                const int q = x / Lw, w = x - q * Lw;
+                s_rows[q * Lw + swz(w)] = __ldcg(from_up + x);
+                s_rows[(nb + 3 + q) * Lw + swz(w)] = __ldcg(from_down + x);
+            }
+            __syncthreads();
+        }
+        if ((k >> 5) != ocall_idx) {
+            ocall_idx = k >> 5;
+            ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
+                                         kTagOffset), rk);
+        }
+        const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
+        switch (o & 3) {
+            case 0: resident_step<0>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
+            case 1: resident_step<1>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
+            case 2: resident_step<2>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
+            default: resident_step<3>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
+        }
+        __syncthreads();
+        // publish the band's top and bottom 3 rows for the neighbours' next step
+        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 0) * edge;
+        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 1) * edge;
+        for (int x = threadIdx.x; x < 3 * Lw; x += kResThreads) {
+            const int q = x / Lw, w = x - q * Lw;
+            __stcg(to_top + x, s_rows[(3 + q) * Lw + swz(w)]);
+            __stcg(to_bot + x, s_rows[(nb + q) * Lw + swz(w)]);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) store_release(&p.ctr[b], static_cast<unsigned int>(j + 1));
+        if ((j & 15) == 15 && p.counts) {
+            unsigned long long c = 0;
+            for (int x = threadIdx.x; x < nb * Lw; x += kResThreads) c += __popc(s_rows[3 * Lw + x]);
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) c += __shfl_down_sync(0xffffffffu, c, s);
+            if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = c;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long tot = 0;
+                for (int w = 0; w < kResThreads / 32; ++w) tot += s_warp[w];
+                atomicAdd(&p.counts[j >> 4], tot);
+            }
+        }
+    }
+    // store the band
+    for (int x = threadIdx.x; x < nb * Lw; x += kResThreads) {
+        const int lr = x / Lw, w = x - lr * Lw;
+        p.lat[static_cast<size_t>(r0 + lr) * Lw + w] = s_rows[(lr + 3) * Lw + swz(w)];
+    }
+}
+
+}  // namespace
+
+// Bands for a lattice of side L: one per SM when every band keeps at least 4 rows and its
+// rows fit the shared memory; 0 when the lattice cannot be resident.
+int resident_bands(int layout, int L, int sms, size_t smem_optin) {
+    if (layout != kPacked || L < 256 || L % 256 != 0 || sms < 1) return 0;
+    int n = sms;
+    while (n > 1 && L / n < 4) --n;
+    const int max_rows = (L + n - 1) / n;
+    const size_t need = sizeof(uint32_t) * (kTableEntries + static_cast<size_t>(max_rows + 6) * (L / 32));
+    return need <= smem_optin ? n : 0;
+}
+
+size_t resident_mailbox_words(int L, int n_bands) { return static_cast<size_t>(n_bands) * 2 * 2 * 3 * (L / 32); }
+
+cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
+    if (a.n_bands < 1 || a.L % 256 != 0) return cudaErrorInvalidValue;
+    ResidentParams p;
+    p.lat = a.lat;
+    p.L = a.L;
+    p.Lw = a.L / 32;
+    p.n_bands = a.n_bands;
+    p.seed = a.seed;
+    p.k0 = a.k0;
+    p.n_mcs = a.n_mcs;
+    p.table = a.table;
+    p.mailbox = a.mailbox;
+    p.ctr = a.ctr;
+    p.counts = a.counts;
+    p.status = a.status;
+    p.spin_limit = a.spin_limit;
+    p.rk = philox_round_keys(a.seed);
+    const int max_rows = (a.L + a.n_bands - 1) / a.n_bands;
+    const size_t smem = sizeof(uint32_t) * (kTableEntries + static_cast<size_t>(max_rows + 6) * p.Lw);
+    cudaError_t e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.ctr, 0, sizeof(unsigned int) * a.n_bands, s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&p};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident), dim3(a.n_bands), dim3(kResThreads),
+                                       args, smem, s);
+}
+
+}  // namespace pgg

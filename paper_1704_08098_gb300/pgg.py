@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libpgg.so")
 
 PGG_OK, PGG_ERR_ARG, PGG_ERR_CUDA, PGG_ERR_OOM, PGG_ERR_TIMEOUT, PGG_ERR_STATE = 0, -1, -2, -3, -4, -5
 U8, BITPACK = 0, 1
-KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, KERNEL_DIRECT = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, KERNEL_DIRECT, KERNEL_RESIDENT = 0, 1, 2, 3, 4
 LAYOUTS = {"u8": U8, "bitpack": BITPACK, U8: U8, BITPACK: BITPACK}
-KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED, "direct": KERNEL_DIRECT}
+KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED, "direct": KERNEL_DIRECT,
+           "resident": KERNEL_RESIDENT}
 
 _lib = None
 
@@ -50,6 +51,7 @@ def _declare(lib):
         "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]),
         "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
+        "pgg_set_spin_limit": (ctypes.c_int, [_vp, ctypes.c_uint]),
         "pgg_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _ip, _ip, _ip, _ip,
                                         ctypes.POINTER(ctypes.c_float)]),
         "pgg_get_threshold_table": (ctypes.c_int, [_vp, _u32p]),
@@ -222,11 +224,15 @@ class Lattice:
         check(self.lib.pgg_set_schedule(self._h, kern, int(steps_per_launch), int(tile_x),
                                         int(tile_y)), "pgg_set_schedule")
 
+    def set_spin_limit(self, limit: int) -> None:
+        check(self.lib.pgg_set_spin_limit(self._h, int(limit)), "pgg_set_spin_limit")
+
     def schedule(self) -> dict:
         v = [ctypes.c_int() for _ in range(4)]
         check(self.lib.pgg_get_schedule(self._h, *[ctypes.byref(x) for x in v]),
               "pgg_get_schedule")
-        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto", KERNEL_DIRECT: "direct"}
+        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto", KERNEL_DIRECT: "direct",
+                 KERNEL_RESIDENT: "resident"}
         return dict(kernel=names[v[0].value], steps_per_launch=v[1].value, tile_x=v[2].value,
                     tile_y=v[3].value)
 
@@ -236,7 +242,8 @@ class Lattice:
         ms = ctypes.c_float()
         check(self.lib.pgg_autotune(self._h, int(n_mcs), *[ctypes.byref(x) for x in v],
                                     ctypes.byref(ms)), "pgg_autotune")
-        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_DIRECT: "direct"}
+        names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_DIRECT: "direct",
+                 KERNEL_RESIDENT: "resident"}
         return dict(kernel=names[v[0].value], steps_per_launch=v[1].value, tile_x=v[2].value,
                     tile_y=v[3].value, ms_per_mcs=float(ms.value))
 

@@ -288,3 +288,45 @@ def test_autotune_restores_state_and_keeps_results(o, pgg, layout, L):
     ref = before.copy()
     want = o.run(ref, 3.85, 0.5, 5, k_before, 6, threads=THREADS)
     assert np.array_equal(counts, want) and np.array_equal(final, ref)
+
+
+@pytest.mark.parametrize("L,n_mcs", [(256, 12), (768, 6), (1024, 8), (4096, 2)])
+def test_resident_kernel(o, pgg, L, n_mcs):
+    want_lat, want_counts = run_oracle(o, L, 3.8, 0.5, 60 + L, n_mcs)
+    got_lat, got_counts, k = run_gpu(pgg, L, 3.8, 0.5, 60 + L, n_mcs, "bitpack", dict(kernel="resident"))
+    assert k == 16 * n_mcs
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+def test_resident_full_size_and_resume(o, pgg):
+    L = 8192
+    want_lat, want_counts = run_oracle(o, L, 3.744, 0.5, 1, 2)
+    with pgg.Lattice(L, 3.744, 0.5, layout="bitpack") as lat:
+        lat.set_schedule("resident")
+        lat.seed(1, 0.5)
+        c1 = lat.step_mcs(1)
+        c2 = lat.step_mcs(1)   # second launch continues from the stored state
+        got, _ = lat.get()
+    assert np.array_equal(np.concatenate([c1, c2]), want_counts)
+    assert np.array_equal(got, want_lat)
+
+
+def test_resident_wait_timeout_is_reported(o, pgg):
+    """A bounded wait that runs out (spin limit 0: every wait gives up at once) returns
+    PGG_ERR_TIMEOUT at the next synchronising call; the context stays usable."""
+    with pgg.Lattice(1024, 3.9, 0.5, layout="bitpack") as lat:
+        lat.set_schedule("resident")
+        lat.seed(3, 0.5)
+        lat.set_spin_limit(0)
+        lat.advance(1)
+        with pytest.raises(pgg.PGGError) as exc:
+            lat.count()
+        assert exc.value.status == pgg.PGG_ERR_TIMEOUT
+        lat.set_spin_limit(1 << 22)
+        lat.seed(3, 0.5)
+        counts = lat.step_mcs(3)
+        got, _ = lat.get()
+    ref = o.init(1024, 3, 0.5)
+    want = o.run(ref, 3.9, 0.5, 3, 0, 3, threads=THREADS)
+    assert np.array_equal(counts, want) and np.array_equal(got, ref)
