@@ -39,6 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 NCU = {
     "direct:386f968aaf80d09d:bitpack:8192:1:4:64": {"alu_warp_inst": 4870544, "dram_bytes": 8450560},
+    "resident:00d875ad8feed491:bitpack:8192:16:152:0": {"alu_warp_inst": 72357977, "dram_bytes": 8456704},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--r", type=float, default=3.744)
     ap.add_argument("--K", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "simple", "tiled", "direct"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "simple", "tiled", "direct", "resident"])
     ap.add_argument("--fuse", type=int, default=1)
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
@@ -83,7 +84,8 @@ def peaks():
 
 def kernel_source_hash(kernel: str) -> str:
     names = {"direct": ["pgg_kernels_direct.cu"], "tiled": ["pgg_kernels_tiled.cu"],
-             "simple": ["pgg_kernels_basic.cu"]}[kernel] + ["pgg_unit.cuh", "pgg_device.cuh"]
+             "simple": ["pgg_kernels_basic.cu"], "resident": ["pgg_kernels_resident.cu"]}[kernel] + \
+        ["pgg_unit.cuh", "pgg_device.cuh"]
     h = hashlib.sha256()
     for n in names:
         h.update(open(os.path.join(ROOT, "paper_1704_08098_gb300", "csrc", n), "rb").read())

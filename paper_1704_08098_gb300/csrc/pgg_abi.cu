@@ -131,7 +131,7 @@ bool tuned_lookup(const pgg_ctx *c, Schedule *out) {
 
 Schedule resolve_schedule(const pgg_ctx *c) {
     Schedule s{c->kernel, c->k_fuse, c->tile_x, c->tile_y};
-    if (s.kernel == PGG_KERNEL_AUTO && tuned_lookup(c, &s)) return s;
+    if (s.kernel == PGG_KERNEL_AUTO) tuned_lookup(c, &s);  // then resolved like an explicit choice
     if (s.kernel == PGG_KERNEL_AUTO) {
         if (pgg::direct_supported(c->layout, c->L)) {
             s = {PGG_KERNEL_DIRECT, 1, 8, 256};

@@ -330,3 +330,25 @@ def test_resident_wait_timeout_is_reported(o, pgg):
     ref = o.init(1024, 3, 0.5)
     want = o.run(ref, 3.9, 0.5, 3, 0, 3, threads=THREADS)
     assert np.array_equal(counts, want) and np.array_equal(got, ref)
+
+
+def test_autotuned_schedule_is_used_by_auto(o, pgg):
+    """After pgg_autotune the AUTO schedule of every context with that (L, layout) resolves to
+    the winner, including kernels whose launch shape is derived at resolution time."""
+    L = 1024
+    with pgg.Lattice(L, 3.9, 0.5, layout="bitpack") as lat:
+        lat.seed(2)
+        best = lat.autotune(1)
+    with pgg.Lattice(L, 3.9, 0.5, layout="bitpack") as lat:
+        assert lat.schedule()["kernel"] == best["kernel"]
+        lat.seed(2)
+        counts = lat.step_mcs(3)
+        got, _ = lat.get()
+    ref = o.init(L, 2, 0.5)
+    want = o.run(ref, 3.9, 0.5, 2, 0, 3, threads=THREADS)
+    assert np.array_equal(counts, want) and np.array_equal(got, ref)
+    for kernel in ("resident", "direct"):
+        with pgg.Lattice(L, 3.9, 0.5, layout="bitpack") as lat:
+            lat.set_schedule(kernel)
+            s = lat.schedule()
+            assert s["kernel"] == kernel and (kernel != "resident" or s["tile_x"] > 0)
