@@ -24,7 +24,7 @@ namespace pgg {
 namespace {
 
 constexpr int kResThreads = 512;
-constexpr int kResUPT = 8;  // words per task: one direction call
+constexpr int kResUPT = 8;  // words per task (a multiple of 8 needs one direction call per 8 words)
 
 struct ResidentParams {
     uint32_t *lat;            // global lattice (read at the start, written at the end)
@@ -80,7 +80,7 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
             wl[q] = row0[q * Lw + swz(wprev)];
             wc[q] = row0[q * Lw + swz(w0)];
         }
-        const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(c), static_cast<uint32_t>(i >> 2), kl, kh), rk);
+        const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(i >> 2), kl, kh), rk);
         UnitCtx u;
         u.k = k;
         u.a = static_cast<uint32_t>(i >> 2);
