@@ -10,8 +10,10 @@
 // All CTAs are co-resident (cooperative launch). Every wait is bounded: after `spin_limit`
 // polls the CTA sets the status word and stops; its neighbours then time out in turn.
 //
-// Per step the work is the direct kernel's: tasks of one sublattice row and 8 words (one
-// direction call), the shared update core of pgg_unit.cuh, in place in shared memory. The
+// Per step the work is the direct kernel's: tasks of one sublattice row and 4 words, the shared
+// update core of pgg_unit.cuh, in place in shared memory. A step first updates the band's
+// interior sublattice rows, whose reads stay inside the band, and only then waits for the
+// neighbours and refreshes the halo for the at most two edge rows: the wait overlaps work. The
 // count after each MCS is the sum of the bands' population counts.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -24,7 +26,7 @@ namespace pgg {
 namespace {
 
 constexpr int kResThreads = 512;
-constexpr int kResUPT = 8;  // words per task (a multiple of 8 needs one direction call per 8 words)
+constexpr int kResUPT = 4;  // words per task; tasks of one run of 8 words share its direction call
 
 struct ResidentParams {
     uint32_t *lat;            // global lattice (read at the start, written at the end)
@@ -43,7 +45,8 @@ struct ResidentParams {
 __device__ __forceinline__ int band_start(int b, int L, int n) { return static_cast<int>((static_cast<long long>(b) * L) / n); }
 
 // Word w of a band row lives at (w ^ ((w >> 5) & 7)): the 32 lanes of a warp, which start
-// tasks 8 words apart, then hit 32 different banks.
+// tasks 4 words apart (words 4c, c = 0..31 of a 128-word stretch), then hit 32 different banks
+// (bank 4 (c mod 8) + c / 8).
 __device__ __forceinline__ int swz(int w) { return w ^ ((w >> 5) & 7); }
 
 __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
@@ -56,20 +59,47 @@ __device__ __forceinline__ void store_release(unsigned int *p, unsigned int v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Sublattice rows of the band (global rows r in [r0, r0 + nb) with r = oi (mod 4)), split
+// into the interior ones, whose reads (rows r-3 .. r+3) stay inside the band, and the at most
+// two edge ones that read halo rows.
+struct BandRows {
+    int first, n_srows, in_lo, in_hi;  // interior = sublattice rows in_lo .. in_hi - 1
+};
+
+__device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
+    BandRows b;
+    b.first = r0 + ((oi - r0) & 3);
+    b.n_srows = b.first < r0 + nb ? (r0 + nb - b.first + 3) >> 2 : 0;
+    if (b.n_srows == 0) {
+        b.in_lo = b.in_hi = 0;
+        return b;
+    }
+    const int last = b.first + 4 * (b.n_srows - 1);
+    b.in_lo = b.first - 3 < r0 ? 1 : 0;
+    b.in_hi = last + 3 >= r0 + nb ? b.n_srows - 1 : b.n_srows;
+    if (b.in_hi < b.in_lo) b.in_hi = b.in_lo;  // one sublattice row that is an edge row at both ends
+    return b;
+}
+
+// Update the interior sublattice rows of the band (edge = false) or its edge rows (edge = true:
+// row 0 when in_lo = 1, row n_srows - 1 when in_hi < n_srows; never the same row twice, since
+// in_hi >= in_lo). Rows of one sublattice step are 4 apart and an update reads 3 rows either
+// side, so the two calls touch disjoint sites and need no barrier between them.
 template <int OJ>
 __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *__restrict__ s_table,
-                                              const PhiloxKeys &rk, int L, int Lw, int r0, int nb,
-                                              uint64_t k, int oi) {
-    // sublattice rows of the band: global rows r in [r0, r0 + nb) with r = oi (mod 4)
-    const int first = r0 + ((oi - r0) & 3);
-    const int n_srows = first < r0 + nb ? (r0 + nb - first + 3) >> 2 : 0;
+                                              const PhiloxKeys &rk, int Lw, int r0, const BandRows &br,
+                                              bool edge, uint64_t k) {
+    // edge: selected row q is 0 or n_srows - 1 (edge_top: whether row 0 is one of them)
+    const bool edge_top = br.in_lo != 0, edge_bot = br.in_hi < br.n_srows;
+    const int n_rows_sel = edge ? static_cast<int>(edge_top) + static_cast<int>(edge_bot) : br.in_hi - br.in_lo;
     const int runs = Lw / kResUPT;
-    const int n_tasks = n_srows * runs;
+    const int n_tasks = n_rows_sel * runs;
     const uint32_t kl = static_cast<uint32_t>(k), kh = static_cast<uint32_t>(k >> 32) | kTagDir;
     for (int t = threadIdx.x; t < n_tasks; t += kResThreads) {
-        const int sr = t / runs;  // runs is a power of two only for power-of-two L; keep exact
-        const int c = t - sr * runs;
-        const int i = first + 4 * sr;            // global row
+        const int q_sel = t / runs;
+        const int sr = edge ? ((q_sel == 0 && edge_top) ? 0 : br.n_srows - 1) : br.in_lo + q_sel;
+        const int c = t - q_sel * runs;
+        const int i = br.first + 4 * sr;         // global row
         const int lr = i - r0 + 3;               // local row (3 halo rows above the band)
         const uint32_t *row0 = s_rows + (lr - 3) * Lw;
         const int w0 = kResUPT * c;
@@ -130,6 +160,20 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const int total = 16 * p.n_mcs;
     for (int j = 0; j < total; ++j) {
         const uint64_t k = p.k0 + static_cast<uint64_t>(j);
+        if ((k >> 5) != ocall_idx) {
+            ocall_idx = k >> 5;
+            ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
+                                         kTagOffset), rk);
+        }
+        const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
+        const BandRows br = band_rows(r0, nb, o >> 2);
+        // interior rows read only the band's own rows: no need to wait for the neighbours
+        switch (o & 3) {
+            case 0: resident_step<0>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            case 1: resident_step<1>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            case 2: resident_step<2>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            default: resident_step<3>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+        }
         if (j > 0) {
             // neighbours finished step j - 1 and published their edge rows
             if (threadIdx.x == 0) {
@@ -156,17 +200,12 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
             }
             __syncthreads();
         }
-        if ((k >> 5) != ocall_idx) {
-            ocall_idx = k >> 5;
-            ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
-                                         kTagOffset), rk);
-        }
-        const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
+        // the at most two edge rows, which read the halo
         switch (o & 3) {
-            case 0: resident_step<0>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
-            case 1: resident_step<1>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
-            case 2: resident_step<2>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
-            default: resident_step<3>(s_rows, s_table, rk, L, Lw, r0, nb, k, o >> 2); break;
+            case 0: resident_step<0>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            case 1: resident_step<1>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            case 2: resident_step<2>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            default: resident_step<3>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
         }
         __syncthreads();
         // publish the band's top and bottom 3 rows for the neighbours' next step
