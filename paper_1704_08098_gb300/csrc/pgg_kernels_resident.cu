@@ -10,7 +10,7 @@
 // All CTAs are co-resident (cooperative launch). Every wait is bounded: after `spin_limit`
 // polls the CTA sets the status word and stops; its neighbours then time out in turn.
 //
-// Per step the work is the direct kernel's: tasks of one sublattice row and 4 words, the shared
+// Per step the work is the direct kernel's: tasks of one sublattice row and 1-4 words, the shared
 // update core of pgg_unit.cuh, in place in shared memory. A step first updates the band's
 // interior sublattice rows, whose reads stay inside the band, and only then waits for the
 // neighbours and refreshes the halo for the at most two edge rows: the wait overlaps work. The
@@ -26,7 +26,7 @@ namespace pgg {
 namespace {
 
 constexpr int kResThreads = 512;
-constexpr int kResUPT = 4;  // words per task; tasks of one run of 8 words share its direction call
+constexpr int kResMaxUPT = 4;  // words per task at most (a task stays inside one 8-word direction call)
 
 struct ResidentParams {
     uint32_t *lat;            // global lattice (read at the start, written at the end)
@@ -45,8 +45,8 @@ struct ResidentParams {
 __device__ __forceinline__ int band_start(int b, int L, int n) { return static_cast<int>((static_cast<long long>(b) * L) / n); }
 
 // Word w of a band row lives at (w ^ ((w >> 5) & 7)): the 32 lanes of a warp, which start
-// tasks 4 words apart (words 4c, c = 0..31 of a 128-word stretch), then hit 32 different banks
-// (bank 4 (c mod 8) + c / 8).
+// tasks u = 1, 2 or 4 words apart (words u c, c = 0..31), then hit 32 different banks (for
+// u = 4: bank 4 (c mod 8) + c / 8; for u = 2: 2c, or 2c - 31 for c >= 16).
 __device__ __forceinline__ int swz(int w) { return w ^ ((w >> 5) & 7); }
 
 __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
@@ -92,7 +92,11 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
     // edge: selected row q is 0 or n_srows - 1 (edge_top: whether row 0 is one of them)
     const bool edge_top = br.in_lo != 0, edge_bot = br.in_hi < br.n_srows;
     const int n_rows_sel = edge ? static_cast<int>(edge_top) + static_cast<int>(edge_bot) : br.in_hi - br.in_lo;
-    const int runs = Lw / kResUPT;
+    // words per task: 4 when that still gives every thread a task, else fewer, so that the small
+    // phases (edge rows, small bands) spread over all warps instead of a few long tasks
+    const int words = n_rows_sel * Lw;
+    const int upt = words >= kResMaxUPT * kResThreads ? kResMaxUPT : (words >= 2 * kResThreads ? 2 : 1);
+    const int runs = Lw / upt;
     const int n_tasks = n_rows_sel * runs;
     const uint32_t kl = static_cast<uint32_t>(k), kh = static_cast<uint32_t>(k >> 32) | kTagDir;
     for (int t = threadIdx.x; t < n_tasks; t += kResThreads) {
@@ -102,7 +106,7 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
         const int i = br.first + 4 * sr;         // global row
         const int lr = i - r0 + 3;               // local row (3 halo rows above the band)
         const uint32_t *row0 = s_rows + (lr - 3) * Lw;
-        const int w0 = kResUPT * c;
+        const int w0 = upt * c;
         const int wprev = w0 == 0 ? Lw - 1 : w0 - 1;
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
@@ -116,7 +120,7 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
         u.a = static_cast<uint32_t>(i >> 2);
         u.msk = kNib;
 #pragma unroll 1
-        for (int w = w0; w < w0 + kResUPT; ++w) {
+        for (int w = w0; w < w0 + upt; ++w) {
             const int wn = w + 1 == Lw ? 0 : w + 1;
 #pragma unroll
             for (int q = 0; q < 7; ++q) wr[q] = row0[q * Lw + swz(wn)];
