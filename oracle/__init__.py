@@ -17,6 +17,12 @@ Parity status of each function (what pins it; the tests live in ``tests/``):
   run / classic_run    absorbing states, order independence, statistical
                        agreement of the two schedules, rho_C = 0.5 at r = 3.98,
                        K = 0.5 (Section V, Fig. 5 caption), extinction below r_c.
+  pair_*               the pairwise game of Section VI: hand-worked payoffs
+                       (tests/golden), bond-by-bond brute force on tiny tori,
+                       closed forms, the radius-2 read set of an update (Section
+                       VI: one line less than the group game), a brute-force
+                       replay of whole steps, equal payoffs = coin flips,
+                       absorbing states, order independence, schedule agreement.
   offset / dir / u     no external pin: they are the stream-layout convention
                        shared by contract with the GPU library (parity unpinned
                        beyond uniformity checks).
@@ -100,6 +106,29 @@ def _declare(lib):
     lib.oracle_classic_run.argtypes = [_u8p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _u64p]
     lib.oracle_classic_run.restype = ctypes.c_int
+    _dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_pair_neighbour_cooperators.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.oracle_pair_neighbour_cooperators.restype = ctypes.c_int
+    lib.oracle_pair_payoff_games.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    lib.oracle_pair_payoff_games.restype = ctypes.c_double
+    lib.oracle_pair_payoff_total.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
+    lib.oracle_pair_payoff_total.restype = ctypes.c_double
+    lib.oracle_pair_update_threshold.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, _dp, ctypes.c_double]
+    lib.oracle_pair_update_threshold.restype = ctypes.c_uint32
+    lib.oracle_pair_elementary_update.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_uint32, _dp, ctypes.c_double]
+    lib.oracle_pair_elementary_update.restype = ctypes.c_int
+    lib.oracle_pair_sublattice_step.argtypes = [_u8p, ctypes.c_int, _dp, ctypes.c_double,
+                                                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                                ctypes.c_int]
+    lib.oracle_pair_sublattice_step.restype = ctypes.c_int64
+    lib.oracle_pair_run.argtypes = [_u8p, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_uint64,
+                                    ctypes.c_uint64, ctypes.c_int64, _u64p, ctypes.c_int, ctypes.c_int]
+    lib.oracle_pair_run.restype = ctypes.c_int
+    lib.oracle_pair_classic_run.argtypes = [_u8p, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_int64, _u64p]
+    lib.oracle_pair_classic_run.restype = ctypes.c_int
     lib.oracle_error_count.argtypes = []
     lib.oracle_error_count.restype = ctypes.c_int
     lib.oracle_clear_errors.argtypes = []
@@ -212,6 +241,70 @@ class Oracle:
                                          _ptr(counts, _u64p))
         if rc != 0:
             raise ValueError("oracle_classic_run rejected the lattice")
+        return counts[:n_mcs]
+
+    # --- the pairwise game (Section VI); pay = (R, S, T, P) ------------------
+    @staticmethod
+    def _pay(pay) -> np.ndarray:
+        a = np.ascontiguousarray(np.asarray(pay, dtype=np.float64))
+        assert a.shape == (4,)
+        return a
+
+    def pair_neighbour_cooperators(self, lat, i: int, j: int) -> int:
+        a = self._lat(lat)
+        return self.lib.oracle_pair_neighbour_cooperators(_ptr(a, _u8p), a.shape[0], i, j)
+
+    def pair_payoff_games(self, lat, i: int, j: int, pay) -> float:
+        a, p = self._lat(lat), self._pay(pay)
+        return self.lib.oracle_pair_payoff_games(_ptr(a, _u8p), a.shape[0], i, j,
+                                                 _ptr(p, ctypes.POINTER(ctypes.c_double)))
+
+    def pair_payoff_total(self, s: int, n: int, pay) -> float:
+        p = self._pay(pay)
+        return self.lib.oracle_pair_payoff_total(s, n, _ptr(p, ctypes.POINTER(ctypes.c_double)))
+
+    def pair_update_threshold(self, lat, i: int, j: int, d: int, pay, K: float) -> int:
+        a, p = self._lat(lat), self._pay(pay)
+        return int(self.lib.oracle_pair_update_threshold(_ptr(a, _u8p), a.shape[0], i, j, d,
+                                                         _ptr(p, ctypes.POINTER(ctypes.c_double)), K))
+
+    def pair_elementary_update(self, lat: np.ndarray, i: int, j: int, d: int, u: int, pay,
+                               K: float) -> int:
+        assert lat.dtype == np.uint8 and lat.flags.c_contiguous
+        p = self._pay(pay)
+        return self.lib.oracle_pair_elementary_update(_ptr(lat, _u8p), lat.shape[0], i, j, d, u,
+                                                      _ptr(p, ctypes.POINTER(ctypes.c_double)), K)
+
+    def pair_sublattice_step(self, lat: np.ndarray, pay, K: float, seed: int, k: int,
+                             reverse: bool = False, threads: int = 1) -> int:
+        assert lat.dtype == np.uint8 and lat.flags.c_contiguous
+        p = self._pay(pay)
+        return int(self.lib.oracle_pair_sublattice_step(_ptr(lat, _u8p), lat.shape[0],
+                                                        _ptr(p, ctypes.POINTER(ctypes.c_double)), K,
+                                                        seed, k, int(reverse), threads))
+
+    def pair_run(self, lat: np.ndarray, pay, K: float, seed: int, k0: int, n_mcs: int,
+                 reverse: bool = False, threads: int = 1) -> np.ndarray:
+        assert lat.dtype == np.uint8 and lat.flags.c_contiguous
+        p = self._pay(pay)
+        counts = np.zeros(max(n_mcs, 1), dtype=np.uint64)
+        rc = self.lib.oracle_pair_run(_ptr(lat, _u8p), lat.shape[0],
+                                      _ptr(p, ctypes.POINTER(ctypes.c_double)), K, seed, k0, n_mcs,
+                                      _ptr(counts, _u64p), int(reverse), threads)
+        if rc != 0:
+            raise ValueError(f"oracle_pair_run rejected L={lat.shape[0]}")
+        return counts[:n_mcs]
+
+    def pair_classic_run(self, lat: np.ndarray, pay, K: float, seed: int, e0: int,
+                         n_mcs: int) -> np.ndarray:
+        assert lat.dtype == np.uint8 and lat.flags.c_contiguous
+        p = self._pay(pay)
+        counts = np.zeros(max(n_mcs, 1), dtype=np.uint64)
+        rc = self.lib.oracle_pair_classic_run(_ptr(lat, _u8p), lat.shape[0],
+                                              _ptr(p, ctypes.POINTER(ctypes.c_double)), K, seed, e0,
+                                              n_mcs, _ptr(counts, _u64p))
+        if rc != 0:
+            raise ValueError("oracle_pair_classic_run rejected the lattice")
         return counts[:n_mcs]
 
     def errors(self) -> int:

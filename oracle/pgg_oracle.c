@@ -28,6 +28,11 @@
  *   - Eq. (4): the cooperator count after every MCS.
  *   - The classic random-sequential dynamics of Section III (a uniformly random
  *     site per elementary step), used only as a statistical reference.
+ *   - Section VI: the same scheme for a game played pairwise, not in groups (the
+ *     prisoner's dilemma is the example named there): every player plays a 2x2
+ *     matrix game with each of its four nearest neighbours. The read set of an
+ *     update then shrinks by one line in every direction (radius 2); the schedule,
+ *     the random stream and the Fermi rule stay the same.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), key = (seed low 32 bits, seed high 32
@@ -50,6 +55,14 @@
  * threshold is formed from P(s, S) in IEEE double precision with no contraction:
  *   D = P(s_x, S_x) - P(s_y, S_y);  W = 1/(1 + exp(D/K));
  *   t = (W >= 1) ? 2^32 - 1 : floor(W * 2^32);  adopt iff s_x != s_y and u < t.
+ *
+ * Pairwise game (reading of Section VI, which names the game but prints no
+ * payoffs): pay = {R, S, T, P} is the payoff of a cooperator meeting a cooperator
+ * (R) or a defector (S), and of a defector meeting a cooperator (T) or a defector
+ * (P). With n the number of cooperators among the four neighbours, the sum over
+ * the four games is P(s, n) = n*A + (4 - n)*B, (A, B) = (R, S) for s = C and
+ * (T, P) for s = D; the oracle sums game by game, checks it against P(s, n) and
+ * forms the threshold from P(s, n) exactly as above.
  *
  * Build: cc -O2 -std=c11 -ffp-contract=off -fPIC -shared [-fopenmp].
  */
@@ -205,6 +218,16 @@ static int g_error = 0;
 int oracle_error_count(void) { return g_error; }
 void oracle_clear_errors(void) { g_error = 0; }
 
+/* The adoption of Eq. (3): x takes the strategy s_y of y iff u < t. */
+static int adopt(uint8_t *lat, int L, int i, int j, int sy, uint32_t t, uint32_t u)
+{
+    if (u < t) {
+        lat[(size_t)i * (size_t)L + (size_t)j] = (uint8_t)sy;
+        return 1;
+    }
+    return 0;
+}
+
 /* Elementary update of Section III for player x = (i, j) and its neighbour in
  * direction dir, with adoption draw u. Returns 1 if x changed strategy. */
 int oracle_elementary_update(uint8_t *lat, int L, int i, int j, int dir, uint32_t u,
@@ -228,11 +251,98 @@ int oracle_elementary_update(uint8_t *lat, int L, int i, int j, int dir, uint32_
         g_error++;
     }
     uint32_t t = oracle_fermi_threshold(px, py, K);
-    if (u < t) {
-        lat[(size_t)i * (size_t)L + (size_t)j] = (uint8_t)sy;
-        return 1;
+    return adopt(lat, L, i, j, sy, t, u);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The pairwise game (Section VI).                                            */
+/* ------------------------------------------------------------------------- */
+
+/* Payoff of one game between a player with strategy s and one with s_other. */
+static double pair_matrix(int s, int s_other, const double pay[4])
+{
+    if (s)
+        return s_other ? pay[0] : pay[1];
+    return s_other ? pay[2] : pay[3];
+}
+
+/* Number of cooperators among the four nearest neighbours of (i, j). */
+int oracle_pair_neighbour_cooperators(const uint8_t *lat, int L, int i, int j)
+{
+    int n = 0;
+    for (int d = 0; d < 4; ++d)
+        n += strategy_at(lat, L, i + NB_DI[d], j + NB_DJ[d]);
+    return n;
+}
+
+/* Payoff of the player at (i, j), game by game over its four neighbours. */
+double oracle_pair_payoff_games(const uint8_t *lat, int L, int i, int j, const double pay[4])
+{
+    int s = strategy_at(lat, L, i, j);
+    double pi = 0.0;
+    for (int d = 0; d < 4; ++d)
+        pi += pair_matrix(s, strategy_at(lat, L, i + NB_DI[d], j + NB_DJ[d]), pay);
+    return pi;
+}
+
+/* The same payoff from the count n of cooperating neighbours. */
+double oracle_pair_payoff_total(int s, int n, const double pay[4])
+{
+    double a = s ? pay[0] : pay[2];
+    double b = s ? pay[1] : pay[3];
+    return (double)n * a + (double)(4 - n) * b;
+}
+
+/* Threshold of the update of x = (i, j) towards its neighbour in direction dir
+ * (0 when the two already agree). */
+uint32_t oracle_pair_update_threshold(const uint8_t *lat, int L, int i, int j, int dir,
+                                      const double pay[4], double K)
+{
+    int yi = i + NB_DI[dir], yj = j + NB_DJ[dir];
+    int sx = strategy_at(lat, L, i, j);
+    int sy = strategy_at(lat, L, yi, yj);
+    if (sx == sy)
+        return 0;
+    int nx = oracle_pair_neighbour_cooperators(lat, L, i, j);
+    int ny = oracle_pair_neighbour_cooperators(lat, L, yi, yj);
+    double px = oracle_pair_payoff_total(sx, nx, pay);
+    double py = oracle_pair_payoff_total(sy, ny, pay);
+    double gx = oracle_pair_payoff_games(lat, L, i, j, pay);
+    double gy = oracle_pair_payoff_games(lat, L, yi, yj, pay);
+    if (fabs(gx - px) > 1e-9 * (1.0 + fabs(px)) || fabs(gy - py) > 1e-9 * (1.0 + fabs(py))) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+        g_error++;
     }
-    return 0;
+    return oracle_fermi_threshold(px, py, K);
+}
+
+/* Elementary update of the pairwise game. Returns 1 if x changed strategy. */
+int oracle_pair_elementary_update(uint8_t *lat, int L, int i, int j, int dir, uint32_t u,
+                                  const double pay[4], double K)
+{
+    int sy = strategy_at(lat, L, i + NB_DI[dir], j + NB_DJ[dir]);
+    if (strategy_at(lat, L, i, j) == sy)
+        return 0;
+    uint32_t t = oracle_pair_update_threshold(lat, L, i, j, dir, pay, K);
+    return adopt(lat, L, i, j, sy, t, u);
+}
+
+/* Which game an update plays: the group game with synergy r, or the pairwise
+ * game with matrix pay. */
+struct game {
+    int pairwise;
+    double r;
+    double pay[4];
+};
+
+static int game_update(uint8_t *lat, int L, int i, int j, int dir, uint32_t u,
+                       const struct game *g, double K)
+{
+    if (g->pairwise)
+        return oracle_pair_elementary_update(lat, L, i, j, dir, u, g->pay, K);
+    return oracle_elementary_update(lat, L, i, j, dir, u, g->r, K);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -268,8 +378,8 @@ uint64_t oracle_count(const uint8_t *lat, int L)
  * order; threads > 1 splits the sublattice rows over OpenMP threads (the sites
  * are independent, so all three give the same lattice). Returns the number of
  * adoptions. */
-int64_t oracle_sublattice_step(uint8_t *lat, int L, double r, double K, uint64_t seed,
-                               uint64_t k, int reverse, int threads)
+static int64_t game_sublattice_step(uint8_t *lat, int L, const struct game *g, double K,
+                                    uint64_t seed, uint64_t k, int reverse, int threads)
 {
     int o = oracle_offset(seed, k);
     int oi = o >> 2, oj = o & 3;
@@ -286,7 +396,7 @@ int64_t oracle_sublattice_step(uint8_t *lat, int L, double r, double K, uint64_t
             int i = 4 * a + oi, j = 4 * b + oj;
             int d = oracle_dir(seed, k, (uint32_t)a, (uint32_t)b);
             uint32_t u = oracle_u(seed, k, (uint32_t)a, (uint32_t)b);
-            changed += oracle_elementary_update(lat, L, i, j, d, u, r, K);
+            changed += game_update(lat, L, i, j, d, u, g, K);
         }
     }
     return changed;
@@ -295,15 +405,15 @@ int64_t oracle_sublattice_step(uint8_t *lat, int L, double r, double K, uint64_t
 /* n_mcs full Monte Carlo steps (16 sublattice steps each) starting at sublattice
  * step k0; counts[m] (if not NULL) receives the cooperator count after MCS m.
  * Returns 0, or -1 for an invalid lattice size. */
-int oracle_run(uint8_t *lat, int L, double r, double K, uint64_t seed, uint64_t k0,
-               int64_t n_mcs, uint64_t *counts, int reverse, int threads)
+static int game_run(uint8_t *lat, int L, const struct game *g, double K, uint64_t seed,
+                    uint64_t k0, int64_t n_mcs, uint64_t *counts, int reverse, int threads)
 {
     if (L < 4 || L % 4 != 0)
         return -1;
     uint64_t k = k0;
     for (int64_t m = 0; m < n_mcs; ++m) {
         for (int s = 0; s < 16; ++s, ++k)
-            oracle_sublattice_step(lat, L, r, K, seed, k, reverse, threads);
+            game_sublattice_step(lat, L, g, K, seed, k, reverse, threads);
         if (counts)
             counts[m] = oracle_count(lat, L);
     }
@@ -315,8 +425,8 @@ int oracle_run(uint8_t *lat, int L, double r, double K, uint64_t seed, uint64_t 
  * L^2 elementary steps form one MCS. Statistical reference only (its stream, tag
  * 5, is not shared with the parallel schedule). e0 is the first elementary-step
  * index. */
-int oracle_classic_run(uint8_t *lat, int L, double r, double K, uint64_t seed, uint64_t e0,
-                       int64_t n_mcs, uint64_t *counts)
+static int game_classic_run(uint8_t *lat, int L, const struct game *g, double K, uint64_t seed,
+                            uint64_t e0, int64_t n_mcs, uint64_t *counts)
 {
     if (L < 3)
         return -1;
@@ -330,12 +440,68 @@ int oracle_classic_run(uint8_t *lat, int L, double r, double K, uint64_t seed, u
             uint64_t x = (uint64_t)(((unsigned __int128)r64 * n) >> 64);
             int i = (int)(x / (uint64_t)L), j = (int)(x % (uint64_t)L);
             int d = (int)(w[2] >> 30);
-            oracle_elementary_update(lat, L, i, j, d, w[3], r, K);
+            game_update(lat, L, i, j, d, w[3], g, K);
         }
         if (counts)
             counts[m] = oracle_count(lat, L);
     }
     return 0;
+}
+
+static struct game group_game(double r)
+{
+    struct game g = {0, r, {0.0, 0.0, 0.0, 0.0}};
+    return g;
+}
+
+static struct game pair_game(const double pay[4])
+{
+    struct game g = {1, 0.0, {pay[0], pay[1], pay[2], pay[3]}};
+    return g;
+}
+
+/* The public goods game (Section III) ... */
+int64_t oracle_sublattice_step(uint8_t *lat, int L, double r, double K, uint64_t seed,
+                               uint64_t k, int reverse, int threads)
+{
+    struct game g = group_game(r);
+    return game_sublattice_step(lat, L, &g, K, seed, k, reverse, threads);
+}
+
+int oracle_run(uint8_t *lat, int L, double r, double K, uint64_t seed, uint64_t k0,
+               int64_t n_mcs, uint64_t *counts, int reverse, int threads)
+{
+    struct game g = group_game(r);
+    return game_run(lat, L, &g, K, seed, k0, n_mcs, counts, reverse, threads);
+}
+
+int oracle_classic_run(uint8_t *lat, int L, double r, double K, uint64_t seed, uint64_t e0,
+                       int64_t n_mcs, uint64_t *counts)
+{
+    struct game g = group_game(r);
+    return game_classic_run(lat, L, &g, K, seed, e0, n_mcs, counts);
+}
+
+/* ... and the pairwise game (Section VI), on the same schedule and stream. */
+int64_t oracle_pair_sublattice_step(uint8_t *lat, int L, const double pay[4], double K,
+                                    uint64_t seed, uint64_t k, int reverse, int threads)
+{
+    struct game g = pair_game(pay);
+    return game_sublattice_step(lat, L, &g, K, seed, k, reverse, threads);
+}
+
+int oracle_pair_run(uint8_t *lat, int L, const double pay[4], double K, uint64_t seed,
+                    uint64_t k0, int64_t n_mcs, uint64_t *counts, int reverse, int threads)
+{
+    struct game g = pair_game(pay);
+    return game_run(lat, L, &g, K, seed, k0, n_mcs, counts, reverse, threads);
+}
+
+int oracle_pair_classic_run(uint8_t *lat, int L, const double pay[4], double K, uint64_t seed,
+                            uint64_t e0, int64_t n_mcs, uint64_t *counts)
+{
+    struct game g = pair_game(pay);
+    return game_classic_run(lat, L, &g, K, seed, e0, n_mcs, counts);
 }
 
 int oracle_max_threads(void)

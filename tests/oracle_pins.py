@@ -304,9 +304,212 @@ def pin_payoff_consistency_during_run(o):
     assert o.errors() == 0
 
 
+# --------------------------------------------------------------------------- #
+# The pairwise game of Section VI (pay = (R, S, T, P))                          #
+# --------------------------------------------------------------------------- #
+PAIR_MATRICES = [(1.0, 0.0, 1.5, 0.0), (3.0, -1.0, 5.0, 0.5), (1.0, 0.25, 1.75, 0.0),
+                 (0.7, -0.3, 1.9, 0.1)]
+
+
+def load_pair_hand_worked():
+    rows = []
+    with open(os.path.join(GOLDEN, "pair_payoffs_hand_worked.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            L, R, S, T, Pp, pat, i, j, n, pay = line.split()
+            rows.append((int(L), (float(R), float(S), float(T), float(Pp)), pat, int(i), int(j),
+                         int(n), float(pay)))
+    return rows
+
+
+def pin_pair_payoff_hand_worked(o):
+    for L, pay, pat, i, j, n, want in load_pair_hand_worked():
+        lat = pattern_lattice(L, pat)
+        s = int(lat[i, j])
+        assert o.pair_neighbour_cooperators(lat, i, j) == n, (L, pat, i, j)
+        assert abs(o.pair_payoff_games(lat, i, j, pay) - want) < 1e-12, (L, pay, pat, i, j, "games")
+        assert abs(o.pair_payoff_total(s, n, pay) - want) < 1e-12, (L, pay, pat, i, j, "total")
+
+
+def brute_force_pair_payoffs(lat: np.ndarray, pay):
+    """Payoffs by enumerating every bond of the torus once (each horizontal bond
+    (i, j)-(i, j+1) and each vertical bond (i, j)-(i+1, j)); both ends of a bond
+    collect their side of the 2x2 game."""
+    R, S, T, Pp = pay
+    M = {(1, 1): R, (1, 0): S, (0, 1): T, (0, 0): Pp}
+    L = lat.shape[0]
+    out = np.zeros((L, L))
+    ncoop = np.zeros((L, L), dtype=np.int64)
+    for i in range(L):
+        for j in range(L):
+            for (a, b) in (((i, j), (i, (j + 1) % L)), ((i, j), ((i + 1) % L, j))):
+                sa, sb = int(lat[a]), int(lat[b])
+                out[a] += M[(sa, sb)]
+                out[b] += M[(sb, sa)]
+                ncoop[a] += sb
+                ncoop[b] += sa
+    return out, ncoop
+
+
+def pin_pair_brute_force(o):
+    rng = np.random.default_rng(4321)
+    for L in (3, 4, 5, 8):
+        for pay in PAIR_MATRICES:
+            lat = (rng.random((L, L)) < 0.5).astype(np.uint8)
+            want, ncoop = brute_force_pair_payoffs(lat, pay)
+            for i in range(L):
+                for j in range(L):
+                    assert o.pair_neighbour_cooperators(lat, i, j) == ncoop[i, j], (L, i, j)
+                    assert abs(o.pair_payoff_games(lat, i, j, pay) - want[i, j]) < 1e-9, (L, pay, i, j)
+                    s = int(lat[i, j])
+                    assert abs(o.pair_payoff_total(s, int(ncoop[i, j]), pay) - want[i, j]) < 1e-9
+
+
+def pin_pair_closed_forms(o):
+    for pay in PAIR_MATRICES:
+        R, S, T, Pp = pay
+        assert abs(o.pair_payoff_games(pattern_lattice(8, "all_c"), 2, 6, pay) - 4 * R) < 1e-12
+        assert abs(o.pair_payoff_games(pattern_lattice(8, "all_d"), 2, 6, pay) - 4 * Pp) < 1e-12
+        for n in range(5):
+            assert abs(o.pair_payoff_total(1, n, pay) - (n * R + (4 - n) * S)) < 1e-12
+            assert abs(o.pair_payoff_total(0, n, pay) - (n * T + (4 - n) * Pp)) < 1e-12
+    assert o.pair_neighbour_cooperators(pattern_lattice(8, "all_c"), 0, 0) == 4
+
+
+def torus_distance(L, a, b):
+    di = abs(a[0] - b[0]) % L
+    dj = abs(a[1] - b[1]) % L
+    return min(di, L - di) + min(dj, L - dj)
+
+
+def pin_pair_read_set(o):
+    """Section VI: a pairwise update needs one line less in every direction than the
+    group game, i.e. the decision for x reads only sites within distance 2 of x
+    (x's and y's neighbours); a site at distance 2 (beyond y) does matter."""
+    rng = np.random.default_rng(77)
+    L, K = 12, 0.5
+    pay = (3.0, -1.0, 5.0, 0.5)
+    NB = [(0, 1), (0, -1), (1, 0), (-1, 0)]
+    checked = far_influence = 0
+    for trial in range(12):
+        lat = (rng.random((L, L)) < 0.5).astype(np.uint8)
+        i, j = int(rng.integers(L)), int(rng.integers(L))
+        for d in range(4):
+            yi, yj = (i + NB[d][0]) % L, (j + NB[d][1]) % L
+            if lat[i, j] == lat[yi, yj]:
+                assert o.pair_update_threshold(lat, i, j, d, pay, K) == 0
+                continue
+            t0 = o.pair_update_threshold(lat, i, j, d, pay, K)
+            for zi in range(L):
+                for zj in range(L):
+                    dist = torus_distance(L, (i, j), (zi, zj))
+                    if dist < 2:
+                        continue
+                    lat[zi, zj] ^= 1
+                    t1 = o.pair_update_threshold(lat, i, j, d, pay, K)
+                    lat[zi, zj] ^= 1
+                    if dist > 2:
+                        assert t1 == t0, (trial, i, j, d, zi, zj)
+                    elif t1 != t0:
+                        far_influence += 1
+            checked += 1
+    assert checked >= 10 and far_influence > 0, (checked, far_influence)
+
+
+def replay_pair_step(o, lat: np.ndarray, pay, K: float, seed: int, k: int) -> np.ndarray:
+    """One sublattice step written out from the stream definitions, with bond-by-bond
+    payoffs from brute_force_pair_payoffs (all sites of a step are independent)."""
+    L = lat.shape[0]
+    NB = [(0, 1), (0, -1), (1, 0), (-1, 0)]
+    pays, _ = brute_force_pair_payoffs(lat, pay)
+    out = lat.copy()
+    off = o.offset(seed, k)
+    for a in range(L // 4):
+        for b in range(L // 4):
+            i, j = 4 * a + (off >> 2), 4 * b + (off & 3)
+            d = o.dir(seed, k, a, b)
+            yi, yj = (i + NB[d][0]) % L, (j + NB[d][1]) % L
+            if lat[i, j] == lat[yi, yj]:
+                continue
+            t = o.threshold(float(pays[i, j]), float(pays[yi, yj]), K)
+            if o.u(seed, k, a, b) < t:
+                out[i, j] = lat[yi, yj]
+    return out
+
+
+def pin_pair_step_brute_force(o):
+    for L, pay, K, seed in ((8, (1.0, 0.0, 1.5, 0.0), 0.1, 5), (12, (3.0, -1.0, 5.0, 0.5), 2.0, 6),
+                            (8, (0.7, -0.3, 1.9, 0.1), 0.5, 7)):
+        lat = o.init(L, seed, 0.5)
+        for k in range(24):
+            want = replay_pair_step(o, lat, pay, K, seed, k)
+            o.pair_sublattice_step(lat, pay, K, seed, k)
+            assert np.array_equal(lat, want), (L, pay, k)
+
+
+def pin_pair_equal_payoffs(o):
+    # R = S = T = P: every payoff difference is 0, so every adoption is a fair coin
+    # flip (W = 1/2 exactly, Eq. (3))
+    rng = np.random.default_rng(5)
+    for c in (0.0, 2.0, -1.5):
+        pay = (c, c, c, c)
+        lat = (rng.random((8, 8)) < 0.5).astype(np.uint8)
+        for i in range(8):
+            for j in range(8):
+                for d in range(4):
+                    t = o.pair_update_threshold(lat, i, j, d, pay, 0.3)
+                    yi, yj = (i + (0, 0, 1, -1)[d]) % 8, (j + (1, -1, 0, 0)[d]) % 8
+                    assert t == (0 if lat[i, j] == lat[yi, yj] else 1 << 31)
+
+
+def pin_pair_absorbing_and_order(o):
+    for name in ("all_c", "all_d"):
+        lat = pattern_lattice(16, name)
+        ref = lat.copy()
+        counts = o.pair_run(lat, (1.0, 0.0, 1.5, 0.0), 0.1, 3, 0, 4)
+        assert np.array_equal(lat, ref) and all(int(c) == int(ref.sum()) for c in counts)
+    for L, seed in ((16, 2), (28, 9)):
+        a = o.init(L, seed, 0.5)
+        b, c = a.copy(), a.copy()
+        pay = (1.0, 0.5, 1.5, 0.0)
+        ca = o.pair_run(a, pay, 0.5, seed, 0, 5)
+        cb = o.pair_run(b, pay, 0.5, seed, 0, 5, reverse=True)
+        cc = o.pair_run(c, pay, 0.5, seed, 0, 5, threads=3)
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+        assert np.array_equal(ca, cb) and np.array_equal(ca, cc)
+        assert int(ca[-1]) == int(a.sum())
+
+
+def pin_pair_payoff_consistency_during_run(o):
+    o.clear_errors()
+    lat = o.init(24, 8, 0.5)
+    o.pair_run(lat, (0.7, -0.3, 1.9, 0.1), 0.5, 8, 0, 4)
+    assert o.errors() == 0
+
+
+def pin_pair_schedules_agree(o):
+    # the sublattice schedule and the classic random-sequential one give the same
+    # stationary density for the pairwise game as well (snowdrift matrix: both
+    # strategies coexist robustly)
+    pay, K, L = (1.0, 0.5, 1.5, 0.0), 0.5, 96
+    sub, cla = [], []
+    for s in (51, 52):
+        lat = o.init(L, s, 0.5)
+        sub.append(float(o.pair_run(lat, pay, K, s, 0, 800, threads=4)[-400:].mean()) / (L * L))
+        lat = o.init(L, s + 10, 0.5)
+        cla.append(float(o.pair_classic_run(lat, pay, K, s + 10, 0, 800)[-400:].mean()) / (L * L))
+    assert abs(np.mean(sub) - np.mean(cla)) < 0.02, (sub, cla)
+    assert 0.2 < np.mean(sub) < 0.6, sub
+
+
 FAST_PINS = [pin_philox_kat, pin_payoff_hand_worked, pin_payoff_brute_force,
              pin_payoff_closed_forms, pin_fermi_threshold, pin_adoption_comparator,
              pin_init_density, pin_absorbing_states, pin_counts_match_lattice,
              pin_schedule_coverage, pin_order_independence, pin_stream_uniformity,
-             pin_payoff_consistency_during_run]
-SLOW_PINS = [pin_paper_density_r398, pin_extinction_below_rc, pin_schedules_agree]
+             pin_payoff_consistency_during_run, pin_pair_payoff_hand_worked, pin_pair_brute_force,
+             pin_pair_closed_forms, pin_pair_read_set, pin_pair_step_brute_force,
+             pin_pair_equal_payoffs, pin_pair_absorbing_and_order,
+             pin_pair_payoff_consistency_during_run]
+SLOW_PINS = [pin_paper_density_r398, pin_extinction_below_rc, pin_schedules_agree,
+             pin_pair_schedules_agree]

@@ -31,6 +31,18 @@ MUTANTS = {
     "philox_word_swap": ("uint32_t n1 = lo1;", "uint32_t n1 = lo0;"),
     "total_misses_one_group": ("for (int d = 0; d < 4; ++d)\n        S += oracle_group_cooperators",
                                "for (int d = 0; d < 3; ++d)\n        S += oracle_group_cooperators"),
+    # the pairwise game (Section VI)
+    "pair_sucker_temptation_swapped": ("return s_other ? pay[0] : pay[1];", "return s_other ? pay[0] : pay[2];"),
+    "pair_total_complement_5": ("(double)(4 - n) * b;", "(double)(5 - n) * b;"),
+    "pair_count_includes_self": ("int n = 0;\n    for (int d = 0; d < 4; ++d)\n        n += strategy_at",
+                                 "int n = strategy_at(lat, L, i, j);\n    for (int d = 0; d < 4; ++d)\n        n += strategy_at"),
+    "pair_defector_row_ignored": ("double a = s ? pay[0] : pay[2];", "double a = pay[0];"),
+    "pair_threshold_args_swapped": ("return oracle_fermi_threshold(px, py, K);",
+                                    "return oracle_fermi_threshold(py, px, K);"),
+    "pair_ny_counted_at_x": ("int ny = oracle_pair_neighbour_cooperators(lat, L, yi, yj);",
+                             "int ny = oracle_pair_neighbour_cooperators(lat, L, i, j);"),
+    "pair_games_skip_one": ("for (int d = 0; d < 4; ++d)\n        pi += pair_matrix",
+                            "for (int d = 0; d < 3; ++d)\n        pi += pair_matrix"),
 }
 
 
