@@ -8,7 +8,7 @@ Bernoulli(1/2) initial state (Section III), seed 1 (+ rank). Inputs are resident
 HBM when the timed region starts; the L2 cache is flushed between timed steps (a
 256 MiB write that the per-step CUDA events exclude).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--game pairwise]
 
 Prints one JSON line. ``--impl reference`` times the CPU oracle (test
 infrastructure, as it stands) on the host cores for the same metric and config.
@@ -64,7 +64,26 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--game", default="group", choices=["group", "pairwise"],
+                    help="group: the public goods game (Section III); pairwise: a 2x2 matrix game "
+                         "with each neighbour (Section VI)")
+    ap.add_argument("--payoff", type=float, nargs=4, default=[1.0, 0.0, 1.04, 0.0],
+                    metavar=("R", "S", "T", "P"), help="pairwise payoff matrix (weak prisoner's dilemma)")
     return ap.parse_args()
+
+
+def game_text(args) -> str:
+    if args.game == "pairwise":
+        return f"pairwise game (R,S,T,P)=({', '.join(f'{x:g}' for x in args.payoff)}), K={args.K}"
+    return f"PGG lattice, r={args.r}, K={args.K}"
+
+
+def oracle_mcs(o, lat, args, k: int, threads: int) -> None:
+    """One MCS of the oracle for the benchmark's game, from sublattice step k."""
+    if args.game == "pairwise":
+        o.pair_run(lat, args.payoff, args.K, args.seed, k, 1, threads=threads)
+    else:
+        o.run(lat, args.r, args.K, args.seed, k, 1, threads=threads)
 
 
 def dist_info():
@@ -240,17 +259,18 @@ def algorithmic_bytes_per_update(layout: str, k: int) -> float:
     return 32.0 * b / k
 
 
-def cpu_baseline(L, r, K, seed, budget_s=12.0):
+def cpu_baseline(args, budget_s=12.0):
     """The CPU oracle, as it stands, on this host's cores: one MCS on the same workload
     (more if it finishes early), timed with a steady clock."""
     import oracle
     o = oracle.Oracle()
     threads = os.cpu_count() or 1
-    lat = o.init(L, seed, 0.5)
+    L = args.L
+    lat = o.init(L, args.seed, 0.5)
     n = 0
     t0 = time.perf_counter()
     while True:
-        o.run(lat, r, K, seed, 16 * n, 1, threads=threads)
+        oracle_mcs(o, lat, args, 16 * n, threads)
         n += 1
         el = time.perf_counter() - t0
         if el > budget_s / 2 or n >= 8:
@@ -271,11 +291,11 @@ def run_reference(args, rank, world):
     lat = o.init(L, args.seed, 0.5)
     k = 0
     for _ in range(args.warmup):
-        o.run(lat, args.r, args.K, args.seed, k, 1, threads=threads)
+        oracle_mcs(o, lat, args, k, threads)
         k += 16
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.run(lat, args.r, args.K, args.seed, k, 1, threads=threads)
+        oracle_mcs(o, lat, args, k, threads)
         k += 16
     el = time.perf_counter() - t0
     value = L * L * args.steps / el
@@ -284,9 +304,10 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": f"L={L} PGG lattice, r={args.r}, K={args.K}, Bernoulli(0.5) "
+        "config": {"workload": f"L={L} {game_text(args)}, Bernoulli(0.5) "
                                f"start, seed {args.seed}; one step = 1 MCS", "L": L,
-                   "layout": "u8 (oracle)", "r": args.r, "K": args.K},
+                   "layout": "u8 (oracle)", "game": args.game, "r": args.r, "K": args.K,
+                   "payoff": args.payoff if args.game == "pairwise" else None},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} timed MCS after {args.warmup} warm-up MCS"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -320,6 +341,8 @@ def main():
 
     L = args.L
     lat = pgg.Lattice(L, args.r, args.K, layout=args.layout, stream=stream.cuda_stream)
+    if args.game == "pairwise":
+        lat.set_game("pairwise", args.payoff)
     lat.seed(args.seed + rank, 0.5)
     tuned = None
     if args.kernel != "auto":
@@ -371,7 +394,8 @@ def main():
     pk, pk_kind = peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz") or 2070.0
-    key = f"{sched['kernel']}:{kernel_source_hash(sched['kernel'])}:{args.layout}:{L}:" \
+    kname = sched["kernel"] + ("-pairwise" if args.game == "pairwise" else "")
+    key = f"{kname}:{kernel_source_hash(sched['kernel'])}:{args.layout}:{L}:" \
           f"{k}:{sched['tile_x']}:{sched['tile_y']}"
     ncu = NCU.get(key)
     alu_peak = sm_count * ALU_LANES_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12  # Tops/s
@@ -417,17 +441,18 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(L, args.r, args.K, args.seed)
+        cpu = cpu_baseline(args)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "u1" if args.layout == "bitpack" else "u8", "data": "synthetic",
-        "config": {"workload": f"L={L} {args.layout} PGG lattice, r={args.r}, K={args.K}, "
+        "config": {"workload": f"L={L} {args.layout} {game_text(args)}, "
                                f"Bernoulli(0.5) start, seed {args.seed}+rank; one step = 1 MCS "
                                f"= {L * L} site updates",
-                   "L": L, "layout": args.layout, "r": args.r, "K": args.K,
+                   "L": L, "layout": args.layout, "game": args.game, "r": args.r, "K": args.K,
+                   "payoff": args.payoff if args.game == "pairwise" else None,
                    "schedule": sched, "autotuned": tuned,
                    "l2": "flushed between timed steps (256 MiB write, "
                                               "excluded by the per-step CUDA events)",

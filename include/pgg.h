@@ -70,12 +70,22 @@ typedef enum {
                         word w = column 32w + b; needs L % 32 == 0 */
 } pgg_layout;
 
+/* The game the lattice plays. */
+typedef enum {
+    PGG_GAME_GROUP = 0,   /* the public goods game in groups of five (Section III, Eq. (1)-(2));
+                             the default */
+    PGG_GAME_PAIRWISE = 1 /* a 2x2 matrix game with each of the four nearest neighbours, e.g.
+                             the prisoner's dilemma (Section VI); an update reads one line
+                             less in every direction (radius 2) */
+} pgg_game;
+
 /* Kernel family used by pgg_step_mcs. */
 typedef enum {
     PGG_KERNEL_AUTO = 0,   /* the tuned default for (L, layout) */
     PGG_KERNEL_SIMPLE = 1, /* one launch per sublattice step, one thread per 8 sites,
                               operands from global memory; the plain baseline */
-    PGG_KERNEL_TILED = 2,  /* shared-memory tiles with a 3k-site halo, k sublattice
+    PGG_KERNEL_TILED = 2,  /* shared-memory tiles with a 3k-site halo (2k for the pairwise
+                              game), k sublattice
                               steps fused per launch (temporal blocking); k = 1 runs in
                               place, k > 1 ping-pongs between two lattice buffers */
     PGG_KERNEL_DIRECT = 3, /* bit-packed lattices with L % 256 == 0 only: one launch per
@@ -98,8 +108,25 @@ typedef enum {
  * until pgg_seed or pgg_set_lattice. *out is set to NULL on failure. */
 int pgg_create(pgg_ctx **out, int L, double r, double K, int layout, void *cuda_stream);
 
-/* Change r and K (rebuilds the threshold table; the lattice is kept). */
+/* Change r and K (rebuilds the threshold table; the lattice is kept). Under
+ * PGG_GAME_PAIRWISE, r is kept but unused. */
 int pgg_set_params(pgg_ctx *ctx, double r, double K);
+
+/* Choose the game (Section VI: the same parallel scheme for a game played pairwise).
+ * PGG_GAME_GROUP ignores payoff (may be NULL). PGG_GAME_PAIRWISE needs payoff = {R, S, T, P}
+ * (4 finite doubles, copied): the payoff of a cooperator meeting a cooperator (R) or a
+ * defector (S), and of a defector meeting a cooperator (T) or a defector (P); the weak
+ * prisoner's dilemma is {1, 0, b, 0}. A player with n cooperating neighbours then earns
+ * n A + (4 - n) B, (A, B) = (R, S) for a cooperator and (T, P) for a defector, evaluated in
+ * IEEE double precision without contraction; the adoption rule (Eq. (3), with the context's
+ * K), the schedule and the random stream are those of the group game, and the threshold
+ * table holds 2x5x5 entries indexed (s_x*5 + n_x)*5 + n_y. Every kernel family supports both
+ * games; the batched and allocation-free entry points play the group game only. The
+ * lattice and step counter are kept; autotuned choices are kept per game. */
+int pgg_set_game(pgg_ctx *ctx, int game, const double payoff[4]);
+
+/* The current game and (nullable) its payoff matrix (zeros for PGG_GAME_GROUP). */
+int pgg_get_game(const pgg_ctx *ctx, int *game, double *payoff_out);
 
 /* Initial condition of Section III: every site independently C with probability p
  * (p = 0.5: "equal probability"), drawn from the Philox stream of `seed`; sets the step
@@ -156,7 +183,8 @@ int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int
                      int *tile_y);
 
 /* Copy the 2*26*26 adoption thresholds to host_out, index (s_x*26 + S_x)*26 + S_y with
- * s_y = 1 - s_x (entries with s_x == s_y are never used). */
+ * s_y = 1 - s_x (entries with s_x == s_y are never used). Under PGG_GAME_PAIRWISE the first
+ * 2*5*5 entries hold the table indexed (s_x*5 + n_x)*5 + n_y and the rest are zero. */
 int pgg_get_threshold_table(const pgg_ctx *ctx, uint32_t *host_out);
 
 /* Device pointer of the lattice (layout as created) and its size in bytes, for callers

@@ -39,6 +39,28 @@ void build_threshold_table(double r, double K, uint32_t *T) {
     }
 }
 
+// The pairwise game of Section VI: a player with n cooperating neighbours (of 4) earns
+// P(s, n) = n A + (4 - n) B over its four games, (A, B) = (R, S) for a cooperator and (T, P)
+// for a defector (pay = {R, S, T, P}); thresholds as above, indexed (s_x*5 + n_x)*5 + n_y.
+// The rest of the 2*26*26 buffer is zero.
+void build_pair_threshold_table(const double pay[4], double K, uint32_t *T) {
+    std::memset(T, 0, sizeof(uint32_t) * pgg::kTableEntries);
+    for (int sx = 0; sx < 2; ++sx) {
+        const int sy = 1 - sx;
+        for (int nx = 0; nx < pgg::kNRange; ++nx) {
+            for (int ny = 0; ny < pgg::kNRange; ++ny) {
+                const double ax = sx ? pay[0] : pay[2], bx = sx ? pay[1] : pay[3];
+                const double ay = sy ? pay[0] : pay[2], by = sy ? pay[1] : pay[3];
+                const double px = static_cast<double>(nx) * ax + static_cast<double>(4 - nx) * bx;
+                const double py = static_cast<double>(ny) * ay + static_cast<double>(4 - ny) * by;
+                const double w = 1.0 / (1.0 + std::exp((px - py) / K));
+                T[(sx * pgg::kNRange + nx) * pgg::kNRange + ny] =
+                    (w >= 1.0) ? 0xFFFFFFFFu : static_cast<uint32_t>(w * 4294967296.0);
+            }
+        }
+    }
+}
+
 }  // namespace pgg
 
 namespace {
@@ -81,6 +103,8 @@ void clear_error() { g_last_error.clear(); }
 struct pgg_ctx {
     int L = 0;
     double r = 0, K = 0;
+    int game = PGG_GAME_GROUP;              // pgg_game
+    double pay[4] = {0.0, 0.0, 0.0, 0.0};   // pairwise payoff matrix {R, S, T, P}
     int layout = PGG_U8;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -117,13 +141,14 @@ struct Schedule {
 
 bool tiled_supported(const pgg_ctx *c) { return c->L >= 64 && c->L % 64 == 0; }
 
-// Schedules chosen by pgg_autotune, per (device, L, layout); consulted by PGG_KERNEL_AUTO.
+// Schedules chosen by pgg_autotune, per (device, L, layout, game); consulted by
+// PGG_KERNEL_AUTO.
 std::mutex g_tuned_mutex;
-std::map<std::tuple<int, int, int>, Schedule> g_tuned;
+std::map<std::tuple<int, int, int, int>, Schedule> g_tuned;
 
 bool tuned_lookup(const pgg_ctx *c, Schedule *out) {
     std::lock_guard<std::mutex> lock(g_tuned_mutex);
-    auto it = g_tuned.find(std::make_tuple(c->device, c->L, c->layout));
+    auto it = g_tuned.find(std::make_tuple(c->device, c->L, c->layout, c->game));
     if (it == g_tuned.end()) return false;
     *out = it->second;
     return true;
@@ -212,6 +237,16 @@ int check_status(pgg_ctx *c) {
     return PGG_OK;
 }
 
+// Rebuild the host table for the context's game and parameters and copy it to the device.
+int upload_table(pgg_ctx *c) {
+    if (c->game == PGG_GAME_PAIRWISE) pgg::build_pair_threshold_table(c->pay, c->K, c->table_h);
+    else pgg::build_threshold_table(c->r, c->K, c->table_h);
+    // the host table is copied by value before the call returns
+    PGG_CUDA(cudaMemcpyAsync(c->table_d, c->table_h, sizeof c->table_h, cudaMemcpyHostToDevice, c->stream));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    return PGG_OK;
+}
+
 bool is_device_pointer(const void *p) {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
@@ -288,10 +323,30 @@ int pgg_set_params(pgg_ctx *c, double r, double K) {
     PGG_CUDA(cudaSetDevice(c->device));
     c->r = r;
     c->K = K;
-    pgg::build_threshold_table(r, K, c->table_h);
-    // the host table is copied by value before the call returns
-    PGG_CUDA(cudaMemcpyAsync(c->table_d, c->table_h, sizeof c->table_h, cudaMemcpyHostToDevice, c->stream));
-    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    return upload_table(c);
+}
+
+int pgg_set_game(pgg_ctx *c, int game, const double payoff[4]) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_set_game: NULL context");
+    if (game != PGG_GAME_GROUP && game != PGG_GAME_PAIRWISE) return fail(PGG_ERR_ARG, "pgg_set_game: unknown game %d", game);
+    if (game == PGG_GAME_PAIRWISE) {
+        if (!payoff) return fail(PGG_ERR_ARG, "pgg_set_game: the pairwise game needs its payoff matrix");
+        for (int q = 0; q < 4; ++q)
+            if (!std::isfinite(payoff[q])) return fail(PGG_ERR_ARG, "pgg_set_game: payoff[%d] is not finite", q);
+    }
+    PGG_CUDA(cudaSetDevice(c->device));
+    c->game = game;
+    for (int q = 0; q < 4; ++q) c->pay[q] = game == PGG_GAME_PAIRWISE ? payoff[q] : 0.0;
+    return upload_table(c);
+}
+
+int pgg_get_game(const pgg_ctx *c, int *game, double *payoff_out) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_get_game: NULL context");
+    if (game) *game = c->game;
+    if (payoff_out)
+        for (int q = 0; q < 4; ++q) payoff_out[q] = c->pay[q];
     return PGG_OK;
 }
 
@@ -330,6 +385,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(resident buffers): %s", cudaGetErrorString(e));
         }
         pgg::ResidentArgs a;
+        a.game = c->game;
         a.lat = static_cast<uint32_t *>(c->lat);
         a.L = c->L;
         a.n_bands = bands;
@@ -379,7 +435,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     for (int64_t m = 0; m < n_mcs; ++m) {
         if (s.kernel == PGG_KERNEL_DIRECT) {
             for (int j = 0; j < 16; ++j) {
-                PGG_CUDA(pgg::launch_step_direct(static_cast<uint32_t *>(c->lat), c->L, c->seed, c->step, c->table_d,
+                PGG_CUDA(pgg::launch_step_direct(c->game, static_cast<uint32_t *>(c->lat), c->L, c->seed, c->step, c->table_d,
                                                  c->running_d, s.tile_x, s.tile_y, c->stream));
                 ++c->step;
             }
@@ -387,13 +443,14 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
                                      cudaMemcpyDeviceToDevice, c->stream));
         } else if (s.kernel == PGG_KERNEL_SIMPLE) {
             for (int j = 0; j < 16; ++j) {
-                PGG_CUDA(pgg::launch_step_simple(c->layout, c->lat, c->L, c->seed, c->step, c->table_d, c->stream));
+                PGG_CUDA(pgg::launch_step_simple(c->layout, c->game, c->lat, c->L, c->seed, c->step, c->table_d, c->stream));
                 ++c->step;
             }
             PGG_CUDA(pgg::launch_popcount(c->lat, c->lat_bytes, c->counts_d + m, c->stream));
         } else {
             for (int j = 0; j < 16; j += s.k) {
                 pgg::TiledArgs a;
+                a.game = c->game;
                 a.src = c->lat;
                 a.dst = s.k == 1 ? c->lat : c->lat_alt;
                 a.L = c->L;
@@ -526,7 +583,7 @@ int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, i
         if (tile_y < 0 || tile_y % 4 != 0) return fail(PGG_ERR_ARG, "pgg_set_schedule: tile_y must be a multiple of 4");
         const int tx = tile_x == 0 ? (c->L >= 1024 ? 1024 : c->L) : (tile_x > c->L ? c->L : tile_x);
         const int ty = tile_y == 0 ? 64 : (tile_y > c->L ? c->L : tile_y);
-        if (pgg::tiled_smem_bytes(c->layout, steps_per_launch, tx, ty) == 0)
+        if (pgg::tiled_smem_bytes(c->layout, c->game, steps_per_launch, tx, ty) == 0)
             return fail(PGG_ERR_ARG, "pgg_set_schedule: tile %dx%d with %d fused steps does not fit in shared memory", tx, ty, steps_per_launch);
     }
     c->kernel = kernel;
@@ -587,7 +644,7 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
         for (int k : {1, 2, 4, 8})
             for (const auto &t : tiles) {
                 if (t[0] > c->L || t[1] > c->L) continue;
-                if (pgg::tiled_smem_bytes(c->layout, k, t[0], t[1]) == 0) continue;
+                if (pgg::tiled_smem_bytes(c->layout, c->game, k, t[0], t[1]) == 0) continue;
                 cand.push_back({PGG_KERNEL_TILED, k, t[0], t[1]});
             }
     }
@@ -649,7 +706,7 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lock(g_tuned_mutex);
-        g_tuned[std::make_tuple(c->device, c->L, c->layout)] = best;
+        g_tuned[std::make_tuple(c->device, c->L, c->layout, c->game)] = best;
     }
     if (kernel) *kernel = best.kernel;
     if (steps_per_launch) *steps_per_launch = best.k;

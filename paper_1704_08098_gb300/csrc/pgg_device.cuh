@@ -24,6 +24,17 @@ constexpr uint32_t kTagU = 4u << 24;
 // Group-count sums S lie in [0, 25]; thresholds are indexed (s_x*26 + S_x)*26 + S_y.
 constexpr int kSRange = 26;
 constexpr int kTableEntries = 2 * kSRange * kSRange;
+// Pairwise game (Section VI): the table is indexed (s_x*5 + n_x)*5 + n_y, n = cooperating
+// neighbours (0..4); it uses the first kPairEntries words of the same buffer.
+constexpr int kNRange = 5;
+constexpr int kPairEntries = 2 * kNRange * kNRange;
+
+// Games the step kernels play: the public goods game in groups (Section III) and the
+// pairwise matrix game (Section VI). kReadRadius: rows / columns an update reads on each
+// side of its site.
+enum Game { kGroupGame = 0, kPairGame = 1 };
+template <int GAME>
+constexpr int kReadRadius = GAME == kPairGame ? 2 : 3;
 
 __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
                                                         uint32_t c3, uint32_t k0, uint32_t k1) {

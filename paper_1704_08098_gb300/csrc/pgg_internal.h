@@ -14,6 +14,9 @@ enum Layout { kU8 = 0, kPacked = 1 };
 // Host-built adoption thresholds of Eq. (3), 2*26*26 entries indexed
 // (s_x*26 + S_x)*26 + S_y (defined in pgg_abi.cu).
 void build_threshold_table(double r, double K, uint32_t *T);
+// The same for the pairwise game of Section VI with payoff matrix pay = {R, S, T, P}:
+// 2*5*5 entries indexed (s_x*5 + n_x)*5 + n_y, the rest of the 2*26*26 buffer zero.
+void build_pair_threshold_table(const double pay[4], double K, uint32_t *T);
 
 // Set / clear the calling thread's pgg_last_error() message (defined in pgg_abi.cu).
 int record_error(int code, const char *message);
@@ -24,7 +27,7 @@ cudaError_t launch_init(int layout, void *lat, int L, uint64_t seed, uint64_t th
                         cudaStream_t s);
 
 // One sublattice step k in place with the per-site baseline kernel.
-cudaError_t launch_step_simple(int layout, void *lat, int L, uint64_t seed, uint64_t k,
+cudaError_t launch_step_simple(int layout, int game, void *lat, int L, uint64_t seed, uint64_t k,
                                const uint32_t *table, cudaStream_t s);
 
 // *out += number of set bits in buf (bytes % 16 == 0, buf 16-byte aligned). A uint8
@@ -43,6 +46,7 @@ cudaError_t launch_normalize(uint8_t *buf, size_t n, cudaStream_t s);
 // src and dst may be equal only when steps == 1. If count_out is not NULL the
 // cooperator count of the result is added to *count_out.
 struct TiledArgs {
+    int game;  // Game (pgg_device.cuh): the halo is read radius x steps
     const void *src;
     void *dst;
     int L;
@@ -61,14 +65,15 @@ cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s);
 // memory, upt (4 or 8) words per thread, blocks of `block` (64, 128 or 256) threads;
 // *running (if not NULL) += the change in the number of cooperators. Needs L % 256 == 0.
 bool direct_supported(int layout, int L);
-cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
+cudaError_t launch_step_direct(int game, uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
                                unsigned long long *running, int upt, int block, cudaStream_t s);
 // Shared memory (bytes) the tiled kernel needs for a configuration; 0 if unsupported.
-size_t tiled_smem_bytes(int layout, int steps, int tile_x, int tile_y);
+size_t tiled_smem_bytes(int layout, int game, int steps, int tile_x, int tile_y);
 
 // Whole bit-packed lattice resident in shared memory for n_mcs MCS (one cooperative launch,
 // one row band per CTA, edge rows exchanged through a mailbox between steps).
 struct ResidentArgs {
+    int game;                     // Game (pgg_device.cuh)
     uint32_t *lat;
     int L;
     int n_bands;

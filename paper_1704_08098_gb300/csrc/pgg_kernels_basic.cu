@@ -5,7 +5,8 @@
 // thread per 8 consecutive sublattice sites of a sublattice row, operands read from
 // global memory with the periodic wrap, group counts by the 13-site stencil
 // S(z) = 5 s_z + 2 (4 nearest) + 2 (4 diagonal) + (4 at distance 2), which is the sum of
-// the cooperator counts of the five groups of z (Section III, Fig. 1).
+// the cooperator counts of the five groups of z (Section III, Fig. 1); for the pairwise
+// game (Section VI) the count of cooperating nearest neighbours instead.
 #include <cuda_runtime.h>
 
 #include "pgg_device.cuh"
@@ -169,7 +170,13 @@ __device__ __forceinline__ int group_count_sum(const Reader &s, int i, int j) {
     return 5 * s(i, j) + 2 * (near + diag) + far;
 }
 
-template <bool kBitPacked>
+// Number of cooperating nearest neighbours of z = (i, j) (the pairwise game, Section VI).
+template <class Reader>
+__device__ __forceinline__ int neighbour_count(const Reader &s, int i, int j) {
+    return s(i - 1, j) + s(i + 1, j) + s(i, j - 1) + s(i, j + 1);
+}
+
+template <bool kBitPacked, int GAME>
 __global__ void __launch_bounds__(256)
     k_step_simple(uint8_t *lat8, uint32_t *latp, int L, uint64_t seed, uint64_t k,
                   const uint32_t *__restrict__ table) {
@@ -198,9 +205,14 @@ __global__ void __launch_bounds__(256)
         const int yj = j + (d == 0 ? 1 : (d == 1 ? -1 : 0));
         const int sx = s(i, j), sy = s(yi, yj);
         if (sx == sy) continue;
-        const int Sx = group_count_sum(s, i, j);
-        const int Sy = group_count_sum(s, yi, yj);
-        const uint32_t t = __ldg(&table[(sx * kSRange + Sx) * kSRange + Sy]);
+        uint32_t t;
+        if constexpr (GAME == kPairGame) {
+            const int nx = neighbour_count(s, i, j), ny = neighbour_count(s, yi, yj);
+            t = __ldg(&table[(sx * kNRange + nx) * kNRange + ny]);
+        } else {
+            const int Sx = group_count_sum(s, i, j), Sy = group_count_sum(s, yi, yj);
+            t = __ldg(&table[(sx * kSRange + Sx) * kSRange + Sy]);
+        }
         uint32_t u;
         if (m < 4) {
             if (!have_lo) { u_lo = draw_u4(seed, k, a, (b0 >> 2)); have_lo = true; }
@@ -251,18 +263,20 @@ cudaError_t launch_init(int layout, void *lat, int L, uint64_t seed, uint64_t th
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_simple(int layout, void *lat, int L, uint64_t seed, uint64_t k,
+cudaError_t launch_step_simple(int layout, int game, void *lat, int L, uint64_t seed, uint64_t k,
                                const uint32_t *table, cudaStream_t s) {
     const int n4 = L >> 2;
     const uint64_t threads = static_cast<uint64_t>(n4) * ((n4 + 7) >> 3);
     const int block = 256;
     const unsigned grid = static_cast<unsigned>((threads + block - 1) / block);
-    if (layout == kU8) {
-        k_step_simple<false><<<grid, block, 0, s>>>(static_cast<uint8_t *>(lat), nullptr, L, seed, k,
-                                                   table);
+    uint8_t *l8 = layout == kU8 ? static_cast<uint8_t *>(lat) : nullptr;
+    uint32_t *lp = layout == kU8 ? nullptr : static_cast<uint32_t *>(lat);
+    if (game == kPairGame) {
+        if (layout == kU8) k_step_simple<false, kPairGame><<<grid, block, 0, s>>>(l8, lp, L, seed, k, table);
+        else k_step_simple<true, kPairGame><<<grid, block, 0, s>>>(l8, lp, L, seed, k, table);
     } else {
-        k_step_simple<true><<<grid, block, 0, s>>>(nullptr, static_cast<uint32_t *>(lat), L, seed, k,
-                                                  table);
+        if (layout == kU8) k_step_simple<false, kGroupGame><<<grid, block, 0, s>>>(l8, lp, L, seed, k, table);
+        else k_step_simple<true, kGroupGame><<<grid, block, 0, s>>>(l8, lp, L, seed, k, table);
     }
     return cudaGetLastError();
 }

@@ -2,7 +2,8 @@
 // read straight from global memory (L1/L2), no shared-memory staging.
 //
 // A step only writes the sites of one sublattice, which are at least 4 apart, and an
-// update reads only the Manhattan ball of radius 3 around its site (Section IV, Fig. 3),
+// update reads only the Manhattan ball of radius 3 around its site (Section IV, Fig. 3;
+// radius 2 for the pairwise game of Section VI, which loads 5 rows instead of 7),
 // so the step can run in place with every thread reading its neighbourhood directly: the
 // only words another thread writes during the step are words of the same sublattice row,
 // and the bits it changes there are never among the bits this thread uses.
@@ -39,7 +40,7 @@ struct DirectParams {
     PhiloxKeys rk;
 };
 
-template <int UPT, int OJ>
+template <int UPT, int OJ, int GAME>
 __device__ __forceinline__ long long direct_body(const DirectParams &p, const PhiloxKeys &rk,
                                                  const uint32_t *__restrict__ s_table, int oi) {
     long long delta = 0;
@@ -54,11 +55,12 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
 #pragma unroll
         for (int q = 0; q < 7; ++q) rowoff[q] = wrap_small(i - 3 + q, p.L) * p.Lw;
         const int wprev = w0 == 0 ? p.Lw - 1 : w0 - 1;
+        // rows the game reads (the pairwise game reads two lines less, Section VI)
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            wl[q] = p.lat[rowoff[q] + wprev];
-            wc[q] = p.lat[rowoff[q] + w0];
+            wl[q] = reads_row<GAME>(q) ? p.lat[rowoff[q] + wprev] : 0u;
+            wc[q] = reads_row<GAME>(q) ? p.lat[rowoff[q] + w0] : 0u;
         }
         const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(a), kl, kh), rk);
         UnitCtx u;
@@ -71,11 +73,11 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
             const int w = w0 + s;
             const int wn = w + 1 == p.Lw ? 0 : w + 1;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) wr[q] = p.lat[rowoff[q] + wn];
+            for (int q = 0; q < 7; ++q) wr[q] = reads_row<GAME>(q) ? p.lat[rowoff[q] + wn] : 0u;
             u.gw = w;
             u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
             uint32_t sx;
-            const uint32_t flips = unit_flips<OJ>(wl, wc, wr, u, rk, s_table, sx);
+            const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
             if (flips) {
                 p.lat[rowoff[3] + w] = wc[3] ^ (flips << OJ);
                 delta += __popc(flips & ~sx) - __popc(flips & sx);
@@ -90,22 +92,23 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
     return delta;
 }
 
-template <int UPT, int BLOCK>
+template <int UPT, int BLOCK, int GAME>
 __global__ void __launch_bounds__(BLOCK, PGG_DIRECT_MIN_BLOCKS) k_step_direct(const __grid_constant__ DirectParams p) {
-    __shared__ uint32_t s_table[kTableEntries];
+    constexpr int kEntries = GAME == kPairGame ? kPairEntries : kTableEntries;
+    __shared__ uint32_t s_table[kEntries];
     __shared__ int s_off;
     __shared__ long long s_warp[BLOCK / 32];
-    for (int t = threadIdx.x; t < kTableEntries; t += blockDim.x) s_table[t] = p.table[t];
+    for (int t = threadIdx.x; t < kEntries; t += blockDim.x) s_table[t] = p.table[t];
     if (threadIdx.x == 0) s_off = draw_offset(p.seed, p.k);
     __syncthreads();
     const PhiloxKeys rk = p.rk;
     const int o = s_off;
     long long delta;
     switch (o & 3) {
-        case 0: delta = direct_body<UPT, 0>(p, rk, s_table, o >> 2); break;
-        case 1: delta = direct_body<UPT, 1>(p, rk, s_table, o >> 2); break;
-        case 2: delta = direct_body<UPT, 2>(p, rk, s_table, o >> 2); break;
-        default: delta = direct_body<UPT, 3>(p, rk, s_table, o >> 2); break;
+        case 0: delta = direct_body<UPT, 0, GAME>(p, rk, s_table, o >> 2); break;
+        case 1: delta = direct_body<UPT, 1, GAME>(p, rk, s_table, o >> 2); break;
+        case 2: delta = direct_body<UPT, 2, GAME>(p, rk, s_table, o >> 2); break;
+        default: delta = direct_body<UPT, 3, GAME>(p, rk, s_table, o >> 2); break;
     }
     if (p.running) {
 #pragma unroll
@@ -120,34 +123,44 @@ __global__ void __launch_bounds__(BLOCK, PGG_DIRECT_MIN_BLOCKS) k_step_direct(co
     }
 }
 
-template <int UPT, int BLOCK>
+template <int UPT, int BLOCK, int GAME>
 int resident_grid() {
     static int grid = 0;  // per instance and process; the library drives one device type
     if (!grid) {
         int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_direct<UPT, BLOCK>, BLOCK, 0) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_direct<UPT, BLOCK, GAME>, BLOCK, 0) != cudaSuccess)
             return 0;
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
 }
 
-template <int UPT, int BLOCK>
+template <int UPT, int BLOCK, int GAME>
 cudaError_t launch_direct_instance(const DirectParams &p, cudaStream_t s) {
-    const int grid = resident_grid<UPT, BLOCK>();
+    const int grid = resident_grid<UPT, BLOCK, GAME>();
     if (!grid) return cudaErrorUnknown;
     const int need = (p.n_tasks + BLOCK - 1) / BLOCK;
-    k_step_direct<UPT, BLOCK><<<need < grid ? need : grid, BLOCK, 0, s>>>(p);
+    k_step_direct<UPT, BLOCK, GAME><<<need < grid ? need : grid, BLOCK, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int GAME>
+cudaError_t launch_direct_game(const DirectParams &p, int upt, int block, cudaStream_t s) {
+    // small blocks spread the step's few tasks evenly over the SMs
+    if (block == 128)
+        return upt == 4 ? launch_direct_instance<4, 128, GAME>(p, s) : launch_direct_instance<8, 128, GAME>(p, s);
+    if (block == 256)
+        return upt == 4 ? launch_direct_instance<4, 256, GAME>(p, s) : launch_direct_instance<8, 256, GAME>(p, s);
+    return upt == 4 ? launch_direct_instance<4, 64, GAME>(p, s) : launch_direct_instance<8, 64, GAME>(p, s);
 }
 
 }  // namespace
 
 bool direct_supported(int layout, int L) { return layout == kPacked && L >= 256 && L % 256 == 0; }
 
-cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
+cudaError_t launch_step_direct(int game, uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
                                unsigned long long *running, int upt, int block, cudaStream_t s) {
     if (L < 256 || L % 256 != 0 || (upt != 4 && upt != 8)) return cudaErrorInvalidValue;
     DirectParams p;
@@ -163,10 +176,8 @@ cudaError_t launch_step_direct(uint32_t *lat, int L, uint64_t seed, uint64_t k, 
     p.table = table;
     p.running = running;
     p.rk = philox_round_keys(seed);
-    // small blocks spread the step's few tasks evenly over the SMs
-    if (block == 128) return upt == 4 ? launch_direct_instance<4, 128>(p, s) : launch_direct_instance<8, 128>(p, s);
-    if (block == 256) return upt == 4 ? launch_direct_instance<4, 256>(p, s) : launch_direct_instance<8, 256>(p, s);
-    return upt == 4 ? launch_direct_instance<4, 64>(p, s) : launch_direct_instance<8, 64>(p, s);
+    return game == kPairGame ? launch_direct_game<kPairGame>(p, upt, block, s)
+                             : launch_direct_game<kGroupGame>(p, upt, block, s);
 }
 
 }  // namespace pgg

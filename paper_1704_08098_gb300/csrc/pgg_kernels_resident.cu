@@ -10,6 +10,9 @@
 // All CTAs are co-resident (cooperative launch). Every wait is bounded: after `spin_limit`
 // polls the CTA sets the status word and stops; its neighbours then time out in turn.
 //
+// The pairwise game (Section VI) runs the same way with its radius-2 update (its halo rows
+// beyond the second are exchanged but never read).
+//
 // Per step the work is the direct kernel's: tasks of one sublattice row and 1-4 words, the shared
 // update core of pgg_unit.cuh, in place in shared memory. A step first updates the band's
 // interior sublattice rows, whose reads stay inside the band, and only then waits for the
@@ -60,13 +63,15 @@ __device__ __forceinline__ void store_release(unsigned int *p, unsigned int v) {
 }
 
 // Sublattice rows of the band (global rows r in [r0, r0 + nb) with r = oi (mod 4)), split
-// into the interior ones, whose reads (rows r-3 .. r+3) stay inside the band, and the at most
-// two edge ones that read halo rows.
+// into the interior ones, whose reads (rows r-R .. r+R, R the game's read radius) stay inside
+// the band, and the at most two edge ones that read halo rows.
 struct BandRows {
     int first, n_srows, in_lo, in_hi;  // interior = sublattice rows in_lo .. in_hi - 1
 };
 
+template <int GAME>
 __device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
+    constexpr int R = kReadRadius<GAME>;
     BandRows b;
     b.first = r0 + ((oi - r0) & 3);
     b.n_srows = b.first < r0 + nb ? (r0 + nb - b.first + 3) >> 2 : 0;
@@ -75,8 +80,8 @@ __device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
         return b;
     }
     const int last = b.first + 4 * (b.n_srows - 1);
-    b.in_lo = b.first - 3 < r0 ? 1 : 0;
-    b.in_hi = last + 3 >= r0 + nb ? b.n_srows - 1 : b.n_srows;
+    b.in_lo = b.first - R < r0 ? 1 : 0;
+    b.in_hi = last + R >= r0 + nb ? b.n_srows - 1 : b.n_srows;
     if (b.in_hi < b.in_lo) b.in_hi = b.in_lo;  // one sublattice row that is an edge row at both ends
     return b;
 }
@@ -85,7 +90,7 @@ __device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
 // row 0 when in_lo = 1, row n_srows - 1 when in_hi < n_srows; never the same row twice, since
 // in_hi >= in_lo). Rows of one sublattice step are 4 apart and an update reads 3 rows either
 // side, so the two calls touch disjoint sites and need no barrier between them.
-template <int OJ>
+template <int OJ, int GAME>
 __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *__restrict__ s_table,
                                               const PhiloxKeys &rk, int Lw, int r0, const BandRows &br,
                                               bool edge, uint64_t k) {
@@ -111,8 +116,8 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            wl[q] = row0[q * Lw + swz(wprev)];
-            wc[q] = row0[q * Lw + swz(w0)];
+            wl[q] = reads_row<GAME>(q) ? row0[q * Lw + swz(wprev)] : 0u;
+            wc[q] = reads_row<GAME>(q) ? row0[q * Lw + swz(w0)] : 0u;
         }
         const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(i >> 2), kl, kh), rk);
         UnitCtx u;
@@ -123,11 +128,11 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
         for (int w = w0; w < w0 + upt; ++w) {
             const int wn = w + 1 == Lw ? 0 : w + 1;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) wr[q] = row0[q * Lw + swz(wn)];
+            for (int q = 0; q < 7; ++q) wr[q] = reads_row<GAME>(q) ? row0[q * Lw + swz(wn)] : 0u;
             u.gw = w;
             u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
             uint32_t sx;
-            const uint32_t flips = unit_flips<OJ>(wl, wc, wr, u, rk, s_table, sx);
+            const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
             if (flips) s_rows[lr * Lw + swz(w)] = wc[3] ^ (flips << OJ);
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
@@ -138,6 +143,7 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
     }
 }
 
+template <int GAME>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_constant__ ResidentParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *s_table = smem;
@@ -170,13 +176,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                                          kTagOffset), rk);
         }
         const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
-        const BandRows br = band_rows(r0, nb, o >> 2);
+        const BandRows br = band_rows<GAME>(r0, nb, o >> 2);
         // interior rows read only the band's own rows: no need to wait for the neighbours
         switch (o & 3) {
-            case 0: resident_step<0>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-            case 1: resident_step<1>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-            case 2: resident_step<2>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-            default: resident_step<3>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
         }
         if (j > 0) {
             // neighbours finished step j - 1 and published their edge rows
@@ -206,10 +212,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         }
         // the at most two edge rows, which read the halo
         switch (o & 3) {
-            case 0: resident_step<0>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-            case 1: resident_step<1>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-            case 2: resident_step<2>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-            default: resident_step<3>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
         }
         __syncthreads();
         // publish the band's top and bottom 3 rows for the neighbours' next step
@@ -278,13 +284,14 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.rk = philox_round_keys(a.seed);
     const int max_rows = (a.L + a.n_bands - 1) / a.n_bands;
     const size_t smem = sizeof(uint32_t) * (kTableEntries + static_cast<size_t>(max_rows + 6) * p.Lw);
-    cudaError_t e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const void *kernel = a.game == kPairGame ? reinterpret_cast<const void *>(k_resident<kPairGame>)
+                                             : reinterpret_cast<const void *>(k_resident<kGroupGame>);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.ctr, 0, sizeof(unsigned int) * a.n_bands, s);
     if (e != cudaSuccess) return e;
     void *args[] = {&p};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_resident), dim3(a.n_bands), dim3(kResThreads),
-                                       args, smem, s);
+    return cudaLaunchCooperativeKernel(kernel, dim3(a.n_bands), dim3(kResThreads), args, smem, s);
 }
 
 }  // namespace pgg

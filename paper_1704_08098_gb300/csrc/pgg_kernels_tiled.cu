@@ -3,10 +3,11 @@
 // One CTA owns a tile of tile_y x tile_x sites. It stages the tile plus a halo in shared
 // memory as bit rows (one bit per site, for both lattice layouts), applies `steps`
 // consecutive sublattice steps there, and writes the interior back. An update reads the
-// Manhattan ball of radius 3 around its site (Section IV, Fig. 3: "three lines outward"),
-// so after step j (0-based) of k only the sites within 3 (k - 1 - j) of the interior are
-// still needed and still correct; the halo is therefore 3k sites wide and the updated
-// region shrinks by 3 per step. Every random draw is keyed by global (step, site), so the
+// Manhattan ball of radius R = 3 around its site (Section IV, Fig. 3: "three lines
+// outward"; R = 2 for the pairwise game, one line less, Section VI), so after step j
+// (0-based) of k only the sites within R (k - 1 - j) of the interior are still needed and
+// still correct; the halo is therefore R k sites wide and the updated region shrinks by R
+// per step. Every random draw is keyed by global (step, site), so the
 // halo copies that several tiles compute redundantly agree bit for bit.
 //
 // Work unit: one 32-column word of one sublattice row. Its 8 sublattice sites sit at bits
@@ -37,7 +38,8 @@ struct TiledParams {
     int steps;
     int tile_x, tile_y;
     int tiles_x, tiles_y;
-    int H, hw;      // halo in sites (3 steps) and in words
+    int R;          // read radius of the game's update (3 groups, 2 pairwise)
+    int H, hw;      // halo in sites (R steps) and in words
     int RP;         // shared-memory column pitch in words (odd, >= tile rows + 2H)
     int dir_slot;   // uint32 words of one step's direction buffer
     int dir_words;  // uint32 words reserved for the two direction buffers
@@ -46,7 +48,7 @@ struct TiledParams {
     PhiloxKeys rk;  // round keys of the seed
 };
 
-__host__ __device__ constexpr int halo_words(int steps) { return (3 * (steps - 1) + 31) / 32 + 1; }
+__host__ __device__ constexpr int halo_words(int steps, int R) { return (R * (steps - 1) + 31) / 32 + 1; }
 
 // 32 bytes of 0/1 -> 32 bits (byte n -> bit n).
 __device__ __forceinline__ uint32_t nibble_of_bytes(uint32_t x) { return ((x * 0x00204081u) >> 21) & 0xFu; }
@@ -80,7 +82,7 @@ struct StepGeom {
 
 __device__ __forceinline__ StepGeom step_geom(const TiledParams &p, int x0w, int ih, int iw, int j, int oi) {
     StepGeom g;
-    const int e = 3 * (p.steps - 1 - j);
+    const int e = p.R * (p.steps - 1 - j);
     const int row_lo = p.H - e;
     g.row_hi = p.H + ih + e;
     g.col_lo = 32 * p.hw - e;
@@ -141,7 +143,7 @@ __device__ __forceinline__ void tile_dirs(const TiledParams &p, const PhiloxKeys
 
 // One sublattice step over the update region of the tile, for column offset OJ. The tile
 // is column-major in shared memory: word (row r, word w) at s_tile[w * RP + r].
-template <int LAYOUT, int BLOCK, int OJ>
+template <int LAYOUT, int BLOCK, int OJ, int GAME>
 __device__ __forceinline__ void tile_step(const TiledParams &p, const PhiloxKeys &rk, uint32_t *s_tile,
                                           const uint32_t *__restrict__ s_table,
                                           const uint32_t *__restrict__ s_dir, int y0, int x0w,
@@ -157,13 +159,14 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, const PhiloxKeys
         const int sr = div_by_magic(t, magic);
         const int w = g.w_lo + (t - sr * g.n_words);
         const int r = g.r_first + 4 * sr;
-        uint32_t *col = s_tile + w * RP + (r - 3);
+        uint32_t *col = s_tile + w * RP + r;
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            wl[q] = col[q - RP];
-            wc[q] = col[q];
-            wr[q] = col[q + RP];
+            // rows r-3 .. r+3; a game reads only rows r-R .. r+R, all inside the staged tile
+            wl[q] = reads_row<GAME>(q) ? col[q - 3 - RP] : 0u;
+            wc[q] = reads_row<GAME>(q) ? col[q - 3] : 0u;
+            wr[q] = reads_row<GAME>(q) ? col[q - 3 + RP] : 0u;
         }
         const int U = x0w - p.hw + w;
         const int grow = wrap_small(y0 - p.H + r, p.L);
@@ -179,10 +182,10 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, const PhiloxKeys
             u.msk = nibble_range((g.col_lo - base + 3) >> 2, (g.col_hi - base + 3) >> 2);
         }
         uint32_t sx;
-        const uint32_t flips = unit_flips<OJ>(wl, wc, wr, u, rk, s_table, sx);
+        const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
         if (flips) {
             const uint32_t nw = wc[3] ^ (flips << OJ);
-            col[3] = nw;
+            col[0] = nw;
             if (in_place) {
                 if (LAYOUT == kPacked) {
                     static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + u.gw] = nw;
@@ -203,7 +206,7 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, const PhiloxKeys
 #define PGG_TILED_MIN_BLOCKS 1
 #endif
 
-template <int LAYOUT, int BLOCK>
+template <int LAYOUT, int BLOCK, int GAME>
 __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(const __grid_constant__ TiledParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *s_table = smem;
@@ -216,7 +219,8 @@ __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(cons
     const PhiloxKeys rk = p.rk;
     const int RP = p.RP;
 
-    for (int t = threadIdx.x; t < kTableEntries; t += BLOCK) s_table[t] = p.table[t];
+    constexpr int kEntries = GAME == kPairGame ? kPairEntries : kTableEntries;
+    for (int t = threadIdx.x; t < kEntries; t += BLOCK) s_table[t] = p.table[t];
     if (threadIdx.x < p.steps) s_off[threadIdx.x] = draw_offset(p.seed, p.k0 + threadIdx.x);
 
     const int n_tiles = p.tiles_x * p.tiles_y;
@@ -226,11 +230,11 @@ __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(cons
         const int y0 = ty * p.tile_y, x0 = tx * p.tile_x;
         const int ih = min(p.tile_y, p.L - y0), iw = min(p.tile_x, p.L - x0);
         const int x0w = x0 >> 5;
-        const int R = ih + 2 * p.H;
+        const int n_rows = ih + 2 * p.H;
         const int Wr = (iw >> 5) + 2 * p.hw;
         __syncthreads();  // offsets ready; the previous tile is fully consumed
         // stage tile + halo as bit rows, column-major
-        for (int r = warp; r < R; r += kWarps) {
+        for (int r = warp; r < n_rows; r += kWarps) {
             const int grow = wrap_small(y0 - p.H + r, p.L);
             int gw = wrap_small(x0w - p.hw + lane, p.Lw);
             for (int w = lane; w < Wr; w += 32) {
@@ -253,10 +257,10 @@ __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(cons
             const int oi = o >> 2;
             const uint32_t *dir_j = s_dir + (j & 1) * p.dir_slot;
             switch (o & 3) {
-                case 0: tile_step<LAYOUT, BLOCK, 0>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
-                case 1: tile_step<LAYOUT, BLOCK, 1>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
-                case 2: tile_step<LAYOUT, BLOCK, 2>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
-                default: tile_step<LAYOUT, BLOCK, 3>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                case 0: tile_step<LAYOUT, BLOCK, 0, GAME>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                case 1: tile_step<LAYOUT, BLOCK, 1, GAME>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                case 2: tile_step<LAYOUT, BLOCK, 2, GAME>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
+                default: tile_step<LAYOUT, BLOCK, 3, GAME>(p, rk, s_tile, s_table, dir_j, y0, x0w, ih, iw, j, oi); break;
             }
             if (j + 1 < p.steps)
                 tile_dirs(p, rk, s_dir + ((j + 1) & 1) * p.dir_slot, y0, x0w, ih, iw, j + 1,
@@ -302,33 +306,33 @@ __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(cons
 }
 
 // Largest region of one step: sublattice rows and call-aligned runs (direction buffer).
-void dir_slot_dims(int steps, int tile_x, int tile_y, int *srows, int *runs) {
-    const int e = 3 * (steps - 1);
+void dir_slot_dims(int steps, int R, int tile_x, int tile_y, int *srows, int *runs) {
+    const int e = R * (steps - 1);
     *srows = (tile_y + 2 * e + 3) / 4 + 1;
     *runs = (tile_x + 2 * e + 31) / 32 / 8 + 3;
 }
 
-int column_pitch(int steps, int tile_y) {
-    const int R = tile_y + 6 * steps;
-    return (R & 1) ? R : R + 1;
+int column_pitch(int steps, int R, int tile_y) {
+    const int rows = tile_y + 2 * R * steps;
+    return (rows & 1) ? rows : rows + 1;
 }
 
-size_t smem_bytes_for(int steps, int tile_x, int tile_y, int *dir_slot, int *dir_words) {
-    const int hw = halo_words(steps);
+size_t smem_bytes_for(int steps, int R, int tile_x, int tile_y, int *dir_slot, int *dir_words) {
+    const int hw = halo_words(steps, R);
     const int Wr = tile_x / 32 + 2 * hw;
     int sr, runs;
-    dir_slot_dims(steps, tile_x, tile_y, &sr, &runs);
+    dir_slot_dims(steps, R, tile_x, tile_y, &sr, &runs);
     const int slot = 4 * sr * runs;  // uint32 words per step
     if (dir_slot) *dir_slot = slot;
     if (dir_words) *dir_words = 2 * slot;
     return sizeof(uint32_t) * (static_cast<size_t>(kTableEntries) + kMaxSteps + 2 * static_cast<size_t>(slot) +
-                               static_cast<size_t>(Wr) * column_pitch(steps, tile_y));
+                               static_cast<size_t>(Wr) * column_pitch(steps, R, tile_y));
 }
 
-template <int LAYOUT>
+template <int LAYOUT, int GAME>
 cudaError_t launch_instance(const TiledParams &p, size_t smem, int grid, cudaStream_t s) {
     constexpr int kBlock = 256;
-    auto kernel = k_step_tiled<LAYOUT, kBlock>;
+    auto kernel = k_step_tiled<LAYOUT, kBlock, GAME>;
     // the opt-in limit covers static plus dynamic shared memory; raise the dynamic
     // limit of this instance only as far as a launch needs
     static size_t configured = 48 * 1024;
@@ -350,10 +354,12 @@ cudaError_t launch_instance(const TiledParams &p, size_t smem, int grid, cudaStr
 
 }  // namespace
 
-size_t tiled_smem_bytes(int layout, int steps, int tile_x, int tile_y) {
+int read_radius(int game) { return game == kPairGame ? kReadRadius<kPairGame> : kReadRadius<kGroupGame>; }
+
+size_t tiled_smem_bytes(int layout, int game, int steps, int tile_x, int tile_y) {
     (void)layout;
     if (steps < 1 || steps > kMaxSteps || tile_x < 64 || tile_x % 64 || tile_y < 4 || tile_y % 4) return 0;
-    const size_t b = smem_bytes_for(steps, tile_x, tile_y, nullptr, nullptr);
+    const size_t b = smem_bytes_for(steps, read_radius(game), tile_x, tile_y, nullptr, nullptr);
     return b <= kMaxSmem ? b : 0;
 }
 
@@ -374,17 +380,21 @@ cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s) {
     p.tile_y = a.tile_y;
     p.tiles_x = (a.L + a.tile_x - 1) / a.tile_x;
     p.tiles_y = (a.L + a.tile_y - 1) / a.tile_y;
-    p.H = 3 * a.steps;
-    p.hw = halo_words(a.steps);
-    p.RP = column_pitch(a.steps, a.tile_y);
+    p.R = read_radius(a.game);
+    p.H = p.R * a.steps;
+    p.hw = halo_words(a.steps, p.R);
+    p.RP = column_pitch(a.steps, p.R, a.tile_y);
     p.table = a.table;
     p.count_out = a.count_out;
     p.rk = philox_round_keys(a.seed);
-    const size_t smem = smem_bytes_for(a.steps, a.tile_x, a.tile_y, &p.dir_slot, &p.dir_words);
+    const size_t smem = smem_bytes_for(a.steps, p.R, a.tile_x, a.tile_y, &p.dir_slot, &p.dir_words);
     if (smem > kMaxSmem) return cudaErrorInvalidValue;
     const int grid = p.tiles_x * p.tiles_y;
-    if (a.layout == kPacked) return launch_instance<kPacked>(p, smem, grid, s);
-    return launch_instance<kU8>(p, smem, grid, s);
+    if (a.game == kPairGame)
+        return a.layout == kPacked ? launch_instance<kPacked, kPairGame>(p, smem, grid, s)
+                                   : launch_instance<kU8, kPairGame>(p, smem, grid, s);
+    return a.layout == kPacked ? launch_instance<kPacked, kGroupGame>(p, smem, grid, s)
+                               : launch_instance<kU8, kGroupGame>(p, smem, grid, s);
 }
 
 }  // namespace pgg

@@ -102,6 +102,7 @@ extern "C" int pgg_step_mcs_noalloc(const void *lattice_in, void *lattice_out, i
     for (int64_t m = 0; m < n_mcs; ++m) {
         for (int half = 0; half < 16 / kFuse; ++half) {
             pgg::TiledArgs a;
+            a.game = pgg::kGroupGame;
             a.src = src;
             a.dst = half == 0 ? static_cast<void *>(scratch) : lattice_out;
             a.L = L;

@@ -136,6 +136,91 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     return flips;
 }
 
+// The pairwise game (Section VI): every player plays a 2x2 game with each of its four
+// nearest neighbours, so its payoff depends only on its strategy and the number of
+// cooperating neighbours n (0..4), and an update reads the Manhattan ball of radius 2 (one
+// line less than the group game; rows q = 1..5 of wl/wc/wr):
+//   n(x)         = Y(0,1) + Y(0,-1) + Y(1,0) + Y(-1,0)
+//   n(y), y = x + (0,1): Y(0,2) + Y(0,0) + Y(1,1) + Y(-1,1), and likewise for the others.
+// The threshold table is indexed (s_x*5 + n_x)*5 + n_y (s_y = 1 - s_x where it is used).
+template <int OJ>
+__device__ __forceinline__ uint32_t unit_flips_pair(const uint32_t (&wl)[7], const uint32_t (&wc)[7],
+                                                    const uint32_t (&wr)[7], const UnitCtx &u,
+                                                    const PhiloxKeys &rk,
+                                                    const uint32_t *__restrict__ s_table, uint32_t &sx_out) {
+#define PGG_Y(DI, DJ) (window<(DJ) + OJ>(wl[(DI) + 3], wc[(DI) + 3], wr[(DI) + 3]) & kNib)
+    uint32_t d = u.d16;
+    d = (d | (d << 8)) & 0x00FF00FFu;
+    d = (d | (d << 4)) & 0x0F0F0F0Fu;
+    d = (d | (d << 2)) & 0x33333333u;
+    const uint32_t lo_b = d & kNib;
+    const uint32_t hi_b = (d >> 1) & kNib;
+    const uint32_t sx = PGG_Y(0, 0);
+    const uint32_t ye = PGG_Y(0, 1), yw = PGG_Y(0, -1), ys = PGG_Y(1, 0), yn = PGG_Y(-1, 0);
+    const uint32_t sy = mux(hi_b, mux(lo_b, ye, yw), mux(lo_b, ys, yn));
+    const uint32_t active = (sx ^ sy) & u.msk;
+    sx_out = sx;
+    if (!active) return 0u;
+
+    const uint32_t nx = ye + yw + ys + yn;
+    const uint32_t yse = PGG_Y(1, 1), ysw = PGG_Y(1, -1), yne = PGG_Y(-1, 1), ynw = PGG_Y(-1, -1);
+    const uint32_t ne = PGG_Y(0, 2) + sx + yse + yne;   // y = (i, j+1)
+    const uint32_t nw = PGG_Y(0, -2) + sx + ysw + ynw;  // y = (i, j-1)
+    const uint32_t ns = PGG_Y(2, 0) + sx + yse + ysw;   // y = (i+1, j)
+    const uint32_t nn = PGG_Y(-2, 0) + sx + yne + ynw;  // y = (i-1, j)
+#undef PGG_Y
+    const uint32_t lo_n = lo_b * 15u, hi_n = hi_b * 15u;
+    const uint32_t ny = mux(hi_n, mux(lo_n, ne, nw), mux(lo_n, ns, nn));
+    // bytes: even sites (m = 0, 2, 4, 6) and odd sites; index 25 s_x + 5 n_x + n_y <= 49
+    const uint32_t Ie = 25u * (sx & 0x01010101u) + 5u * (nx & kLowNib) + (ny & kLowNib);
+    const uint32_t Io = 25u * ((sx >> 4) & 0x01010101u) + 5u * ((nx >> 4) & kLowNib) + ((ny >> 4) & kLowNib);
+
+    const uint32_t g0 = 2u * static_cast<uint32_t>(u.gw);
+    const uint32_t kl = static_cast<uint32_t>(u.k), kh = static_cast<uint32_t>(u.k >> 32) | kTagU;
+    uint4 u0 = make_uint4(g0, u.a, kl, kh), u1 = make_uint4(g0 + 1u, u.a, kl, kh);
+    const bool need0 = (active & 0x0000FFFFu) != 0, need1 = (active & 0xFFFF0000u) != 0;
+    if (need0 && need1) {
+        philox_rk2(u0, u1, rk);
+    } else {
+        const uint4 r = philox_rk(need0 ? u0 : u1, rk);
+        if (need0) u0 = r; else u1 = r;
+    }
+
+    uint32_t flips = 0;
+#define PGG_SITE(M, IREG, BYTE, UW)                                                 \
+    {                                                                               \
+        const uint32_t bit = 1u << (4 * (M));                                       \
+        const uint32_t idx = (IREG >> (8 * (BYTE))) & 0xFFu;                        \
+        const uint32_t t = (active & bit) ? s_table[idx] : 0u;                      \
+        flips |= ((UW) < t) ? bit : 0u;                                             \
+    }
+    PGG_SITE(0, Ie, 0, u0.x)
+    PGG_SITE(1, Io, 0, u0.y)
+    PGG_SITE(2, Ie, 1, u0.z)
+    PGG_SITE(3, Io, 1, u0.w)
+    PGG_SITE(4, Ie, 2, u1.x)
+    PGG_SITE(5, Io, 2, u1.y)
+    PGG_SITE(6, Ie, 3, u1.z)
+    PGG_SITE(7, Io, 3, u1.w)
+#undef PGG_SITE
+    return flips;
+}
+
+template <int OJ, int GAME>
+__device__ __forceinline__ uint32_t game_flips(const uint32_t (&wl)[7], const uint32_t (&wc)[7],
+                                               const uint32_t (&wr)[7], const UnitCtx &u,
+                                               const PhiloxKeys &rk,
+                                               const uint32_t *__restrict__ s_table, uint32_t &sx_out) {
+    if constexpr (GAME == kPairGame) return unit_flips_pair<OJ>(wl, wc, wr, u, rk, s_table, sx_out);
+    else return unit_flips<OJ>(wl, wc, wr, u, rk, s_table, sx_out);
+}
+
+// Rows q (0..6, row offsets -3..+3) a game's update reads.
+template <int GAME>
+__host__ __device__ constexpr bool reads_row(int q) {
+    return q >= 3 - kReadRadius<GAME> && q <= 3 + kReadRadius<GAME>;
+}
+
 // Periodic wrap of an index that may be a few periods outside [0, m).
 __device__ __forceinline__ int wrap_small(int v, int m) {
     while (v < 0) v += m;

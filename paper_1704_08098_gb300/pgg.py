@@ -18,6 +18,9 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libpgg.so")
 PGG_OK, PGG_ERR_ARG, PGG_ERR_CUDA, PGG_ERR_OOM, PGG_ERR_TIMEOUT, PGG_ERR_STATE = 0, -1, -2, -3, -4, -5
 U8, BITPACK = 0, 1
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, KERNEL_DIRECT, KERNEL_RESIDENT = 0, 1, 2, 3, 4
+GAME_GROUP, GAME_PAIRWISE = 0, 1
+GAMES = {"group": GAME_GROUP, "pairwise": GAME_PAIRWISE, GAME_GROUP: GAME_GROUP,
+         GAME_PAIRWISE: GAME_PAIRWISE}
 LAYOUTS = {"u8": U8, "bitpack": BITPACK, U8: U8, BITPACK: BITPACK}
 KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED, "direct": KERNEL_DIRECT,
            "resident": KERNEL_RESIDENT}
@@ -42,6 +45,8 @@ def _declare(lib):
         "pgg_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, _vp]),
         "pgg_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
+        "pgg_set_game": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+        "pgg_get_game": (ctypes.c_int, [_vp, _ip, ctypes.POINTER(ctypes.c_double)]),
         "pgg_seed": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double]),
         "pgg_step_mcs": (ctypes.c_int, [_vp, ctypes.c_int64, _vp]),
         "pgg_count_coop": (ctypes.c_int, [_vp, _u64p]),
@@ -167,6 +172,24 @@ class Lattice:
     # -- ABI calls -------------------------------------------------------------
     def set_params(self, r: float, K: float) -> None:
         check(self.lib.pgg_set_params(self._h, float(r), float(K)), "pgg_set_params")
+
+    def set_game(self, game="group", payoff=None) -> None:
+        """pgg_set_game: "group" (the default) or "pairwise" with payoff = (R, S, T, P)."""
+        g = GAMES[game]
+        if payoff is None:
+            ptr = None
+        else:
+            pay = np.ascontiguousarray(np.asarray(payoff, dtype=np.float64))
+            assert pay.shape == (4,)
+            ptr = pay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        check(self.lib.pgg_set_game(self._h, g, ptr), "pgg_set_game")
+
+    def game(self) -> tuple[str, tuple]:
+        g = ctypes.c_int()
+        pay = np.zeros(4, dtype=np.float64)
+        check(self.lib.pgg_get_game(self._h, ctypes.byref(g),
+                                    pay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "pgg_get_game")
+        return ("pairwise" if g.value == GAME_PAIRWISE else "group"), tuple(float(x) for x in pay)
 
     def seed(self, seed: int, p: float = 0.5) -> None:
         check(self.lib.pgg_seed(self._h, int(seed), float(p)), "pgg_seed")

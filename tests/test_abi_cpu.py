@@ -51,6 +51,8 @@ def test_argument_validation_without_gpu(lib):
     assert h.value is None
     assert lib.pgg_seed(None, 1, 0.5) == pgg.PGG_ERR_ARG
     assert lib.pgg_step_mcs(None, 1, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_set_game(None, pgg.GAME_PAIRWISE, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_get_game(None, None, None) == pgg.PGG_ERR_ARG
     lib.pgg_destroy(None)
     assert lib.pgg_version().decode().startswith("pgg-gb300")
 
