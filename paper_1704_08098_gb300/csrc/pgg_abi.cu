@@ -229,6 +229,9 @@ int check_status(pgg_ctx *c) {
         PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
         PGG_CUDA(cudaStreamSynchronize(c->stream));
         c->running_valid = false;
+        if (st == 2)
+            return fail(PGG_ERR_CUDA, "the resident kernel found its shared rows or the mailbox not 16-byte aligned "
+                                      "and did not run; the lattice is unchanged");
         return fail(PGG_ERR_TIMEOUT,
                     "a resident-kernel CTA waited longer than %u polls for a neighbour; the lattice is not "
                     "a valid state (restore it with pgg_set_lattice or pgg_seed)",

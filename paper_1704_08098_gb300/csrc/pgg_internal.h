@@ -83,7 +83,7 @@ struct ResidentArgs {
     uint32_t *mailbox;            // resident_mailbox_words(L, n_bands) words
     unsigned int *ctr;            // n_bands counters
     unsigned long long *counts;   // n_mcs counts, zeroed by the caller
-    int *status;                  // set to 1 if a bounded wait ran out
+    int *status;                  // set to 1 if a bounded wait ran out, 2 if the alignment check failed
     unsigned int spin_limit;      // polls before a wait gives up
 };
 int resident_bands(int layout, int L, int sms, size_t smem_optin);

@@ -6,9 +6,15 @@
 // an update reads rows i-3 .. i+3 (Section IV, Fig. 3), so within a step no CTA needs data a
 // neighbour writes in that step; between steps each CTA publishes its 3 top and 3 bottom band
 // rows to a double-buffered mailbox in global memory, bumps its step counter, and before the
-// next step waits for both neighbours' counters and copies their edge rows into its halo.
+// edge rows of the next step waits for both neighbours' counters and their rows in its halo.
 // All CTAs are co-resident (cooperative launch). Every wait is bounded: after `spin_limit`
 // polls the CTA sets the status word and stops; its neighbours then time out in turn.
+//
+// The exchange runs beside the computation: one extra warp per CTA polls the neighbours'
+// counters, fetches their edge rows into the halo with TMA bulk copies (cp.async.bulk,
+// completion on an mbarrier) and, after each step, bulk-stores the band's own edge rows and
+// releases its counter, while the 16 compute warps update the interior rows; the compute
+// warps wait on the mbarrier only before the edge rows.
 //
 // The pairwise game (Section VI) runs the same way with its radius-2 update (its halo rows
 // beyond the second are exchanged but never read).
@@ -28,7 +34,8 @@
 namespace pgg {
 namespace {
 
-constexpr int kResThreads = 512;
+constexpr int kComputeThreads = 512;                 // warps that update the band
+constexpr int kResThreads = kComputeThreads + 32;     // plus one warp that exchanges halos
 constexpr int kResMaxUPT = 4;  // words per task at most (a task stays inside one 8-word direction call)
 
 struct ResidentParams {
@@ -100,11 +107,11 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
     // words per task: 4 when that still gives every thread a task, else fewer, so that the small
     // phases (edge rows, small bands) spread over all warps instead of a few long tasks
     const int words = n_rows_sel * Lw;
-    const int upt = words >= kResMaxUPT * kResThreads ? kResMaxUPT : (words >= 2 * kResThreads ? 2 : 1);
+    const int upt = words >= kResMaxUPT * kComputeThreads ? kResMaxUPT : (words >= 2 * kComputeThreads ? 2 : 1);
     const int runs = Lw / upt;
     const int n_tasks = n_rows_sel * runs;
     const uint32_t kl = static_cast<uint32_t>(k), kh = static_cast<uint32_t>(k >> 32) | kTagDir;
-    for (int t = threadIdx.x; t < n_tasks; t += kResThreads) {
+    for (int t = threadIdx.x; t < n_tasks; t += kComputeThreads) {
         const int q_sel = t / runs;
         const int sr = edge ? ((q_sel == 0 && edge_top) ? 0 : br.n_srows - 1) : br.in_lo + q_sel;
         const int c = t - q_sel * runs;
@@ -143,108 +150,206 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
     }
 }
 
+// --- TMA bulk copies and the CTA's mbarrier (PTX) ------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// global -> shared, completion counted in bytes on the mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// shared -> global in the thread's bulk async-group
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit_and_wait() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Barrier of the compute warps only (the communication warp does not take part).
+__device__ __forceinline__ void compute_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kComputeThreads) : "memory"); }
+
+// try_wait calls a compute warp makes on the halo mbarrier before it gives up (each call may
+// suspend the thread for a short time; a bulk copy from L2 lands within microseconds).
+constexpr unsigned int kMbarTries = 1u << 26;
+
 template <int GAME>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_constant__ ResidentParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *s_table = smem;
     uint32_t *s_rows = smem + kTableEntries;
-    __shared__ int s_abort;
-    __shared__ unsigned long long s_warp[kResThreads / 32];
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ volatile int s_abort;
+    __shared__ unsigned long long s_warp[kComputeThreads / 32];
+    const int tid = threadIdx.x;
+    const bool comm = tid >= kComputeThreads;  // the last warp exchanges halos, the others compute
     const int b = blockIdx.x, nbnd = p.n_bands;
     const int L = p.L, Lw = p.Lw;
     const int r0 = band_start(b, L, nbnd), nb = band_start(b + 1, L, nbnd) - r0;
     const int up = (b + nbnd - 1) % nbnd, down = (b + 1) % nbnd;
-    const size_t edge = static_cast<size_t>(3) * Lw;  // words of 3 rows
+    const size_t edge = static_cast<size_t>(3) * Lw;                  // words of 3 rows
+    const uint32_t edge_bytes = static_cast<uint32_t>(edge * sizeof(uint32_t));
     const PhiloxKeys rk = p.rk;
-    for (int t = threadIdx.x; t < kTableEntries; t += kResThreads) s_table[t] = p.table[t];
-    if (threadIdx.x == 0) s_abort = 0;
+    // bulk copies need 16-byte aligned rows (the same answer in every CTA: all stop together)
+    if ((smem_u32(s_rows) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u) {
+        if (tid == 0) atomicExch(p.status, 2);
+        return;
+    }
+    for (int t = tid; t < kTableEntries; t += kResThreads) s_table[t] = p.table[t];
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(&s_mbar, 1);
+    }
     // stage band + halo (rows r0 - 3 .. r0 + nb + 2, periodic)
-    for (int x = threadIdx.x; x < (nb + 6) * Lw; x += kResThreads) {
+    for (int x = tid; x < (nb + 6) * Lw; x += kResThreads) {
         const int lr = x / Lw, w = x - lr * Lw;
         const int g = wrap_small(r0 - 3 + lr, L);
         s_rows[lr * Lw + swz(w)] = p.lat[static_cast<size_t>(g) * Lw + w];
     }
+    fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
     __syncthreads();
     uint4 ocall = make_uint4(0, 0, 0, 0);
     uint64_t ocall_idx = ~0ull;
     const int total = 16 * p.n_mcs;
+    bool load_pending = false;  // communication lane: a halo load not yet seen complete
     for (int j = 0; j < total; ++j) {
         const uint64_t k = p.k0 + static_cast<uint64_t>(j);
-        if ((k >> 5) != ocall_idx) {
-            ocall_idx = k >> 5;
-            ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
-                                         kTagOffset), rk);
-        }
-        const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
-        const BandRows br = band_rows<GAME>(r0, nb, o >> 2);
-        // interior rows read only the band's own rows: no need to wait for the neighbours
-        switch (o & 3) {
-            case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-            case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-            case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-            default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-        }
-        if (j > 0) {
-            // neighbours finished step j - 1 and published their edge rows
-            if (threadIdx.x == 0) {
+        if (comm) {
+            // fetch the neighbours' rows after step j - 1 into the halo, asynchronously
+            if (tid == kComputeThreads && j > 0) {
                 unsigned int it = 0;
                 while ((load_acquire(&p.ctr[up]) < static_cast<unsigned int>(j) ||
                         load_acquire(&p.ctr[down]) < static_cast<unsigned int>(j)) && it < p.spin_limit) {
-                    __nanosleep(64);
+                    __nanosleep(32);
                     ++it;
                 }
                 if (it >= p.spin_limit) {
                     atomicExch(p.status, 1);
                     s_abort = 1;
+                } else {
+                    const int par = (j - 1) & 1;
+                    const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * edge;
+                    const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * edge;
+                    fence_async_global();  // the acquired rows, for the async proxy's reads
+                    mbar_expect_tx(&s_mbar, 2 * edge_bytes);
+                    bulk_load(s_rows, from_up, edge_bytes, &s_mbar);
+                    bulk_load(s_rows + static_cast<size_t>(nb + 3) * Lw, from_down, edge_bytes, &s_mbar);
+                    load_pending = true;
                 }
             }
-            __syncthreads();
-            if (s_abort) return;  // no copies in flight; the lattice in global memory is left as it was
-            const int par = (j - 1) & 1;
-            const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * edge;   // its bottom rows
-            const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * edge; // its top rows
-            for (int x = threadIdx.x; x < 3 * Lw; x += kResThreads) {
-                const int q = x / Lw, w = x - q * Lw;
-                s_rows[q * Lw + swz(w)] = __ldcg(from_up + x);
-                s_rows[(nb + 3 + q) * Lw + swz(w)] = __ldcg(from_down + x);
+            __syncwarp();
+        } else {
+            if ((k >> 5) != ocall_idx) {
+                ocall_idx = k >> 5;
+                ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
+                                             kTagOffset), rk);
             }
-            __syncthreads();
-        }
-        // the at most two edge rows, which read the halo
-        switch (o & 3) {
-            case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-            case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-            case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-            default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+            const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
+            const BandRows br = band_rows<GAME>(r0, nb, o >> 2);
+            // interior rows read only the band's own rows: they run while the halo is in flight
+            switch (o & 3) {
+                case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+                case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+                case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+                default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+            }
+            bool ready = true;
+            if (j > 0) {
+                unsigned int it = 0;
+                while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>((j - 1) & 1))) {
+                    if (s_abort || ++it >= kMbarTries) {
+                        ready = false;
+                        break;
+                    }
+                }
+            }
+            if (ready) {
+                // the at most two edge rows, which read the halo
+                switch (o & 3) {
+                    case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+                    case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+                    case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+                    default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+                }
+            } else {
+                s_abort = 1;
+            }
+            fence_async_shared();  // this thread's lattice writes, for the bulk store below
         }
         __syncthreads();
-        // publish the band's top and bottom 3 rows for the neighbours' next step
-        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 0) * edge;
-        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 1) * edge;
-        for (int x = threadIdx.x; x < 3 * Lw; x += kResThreads) {
-            const int q = x / Lw, w = x - q * Lw;
-            __stcg(to_top + x, s_rows[(3 + q) * Lw + swz(w)]);
-            __stcg(to_bot + x, s_rows[(nb + q) * Lw + swz(w)]);
+        if (s_abort) {
+            // a wait ran out: make sure no bulk copy still targets this CTA's shared memory,
+            // then stop; the lattice in global memory is left as it was
+            if (tid == kComputeThreads && load_pending) {
+                unsigned int it = 0;
+                while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>((j - 1) & 1)) && ++it < kMbarTries) {
+                }
+            }
+            return;
         }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) store_release(&p.ctr[b], static_cast<unsigned int>(j + 1));
-        if ((j & 15) == 15 && p.counts) {
+        load_pending = false;
+        if (comm) {
+            // publish the band's top and bottom 3 rows (as laid out in shared memory) for the
+            // neighbours' next step; the compute warps meanwhile start step j + 1, which
+            // writes neither
+            if (tid == kComputeThreads) {
+                uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 0) * edge;
+                uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 1) * edge;
+                bulk_store(to_top, s_rows + static_cast<size_t>(3) * Lw, edge_bytes);
+                bulk_store(to_bot, s_rows + static_cast<size_t>(nb) * Lw, edge_bytes);
+                bulk_commit_and_wait();
+                fence_async_global();
+                __threadfence();
+                store_release(&p.ctr[b], static_cast<unsigned int>(j + 1));
+            }
+            __syncwarp();
+        } else if ((j & 15) == 15 && p.counts) {
             unsigned long long c = 0;
-            for (int x = threadIdx.x; x < nb * Lw; x += kResThreads) c += __popc(s_rows[3 * Lw + x]);
+            for (int x = tid; x < nb * Lw; x += kComputeThreads) c += __popc(s_rows[3 * Lw + x]);
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) c += __shfl_down_sync(0xffffffffu, c, s);
-            if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = c;
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            if ((tid & 31) == 0) s_warp[tid >> 5] = c;
+            compute_barrier();
+            if (tid == 0) {
                 unsigned long long tot = 0;
-                for (int w = 0; w < kResThreads / 32; ++w) tot += s_warp[w];
+                for (int w = 0; w < kComputeThreads / 32; ++w) tot += s_warp[w];
                 atomicAdd(&p.counts[j >> 4], tot);
             }
         }
     }
+    __syncthreads();  // the last bulk store has completed (its issuer waited) before the band is stored
     // store the band
-    for (int x = threadIdx.x; x < nb * Lw; x += kResThreads) {
+    for (int x = tid; x < nb * Lw; x += kResThreads) {
         const int lr = x / Lw, w = x - lr * Lw;
         p.lat[static_cast<size_t>(r0 + lr) * Lw + w] = s_rows[(lr + 3) * Lw + swz(w)];
     }
