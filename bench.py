@@ -424,21 +424,27 @@ def main():
 
     # end to end through the public API with host buffers: upload the lattice from pinned
     # memory, run one MCS, read the count back
+    # (bit-packed lattices travel in their packed form, L*L/8 bytes)
     e2e = None
     if not args.no_e2e:
-        host_lat, _ = lat.get()
-        pinned = torch.from_numpy(host_lat.reshape(-1)).pin_memory()
+        if args.layout == "bitpack":
+            host_words, _ = lat.get_packed()
+            pinned = torch.from_numpy(host_words.reshape(-1).view(np.int32)).pin_memory()
+            upload, h2d, how = lat.set_packed_from_pointer, L * L // 8, "pgg_set_lattice_packed(pinned host, L*L/8 bytes)"
+        else:
+            host_lat, _ = lat.get()
+            pinned = torch.from_numpy(host_lat.reshape(-1)).pin_memory()
+            upload, h2d, how = lat.set_from_pointer, L * L, "pgg_set_lattice(pinned host, L*L bytes)"
         counts = np.zeros(1, dtype=np.uint64)
         reps = max(3, min(args.steps, 10))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
-            lat.set_from_pointer(pinned.data_ptr(), 0)
+            upload(pinned.data_ptr(), 0)
             lat.step_mcs(1, counts)
         el = time.perf_counter() - t0
-        e2e = {"value": L * L * reps / el, "unit": UNIT, "h2d_bytes_per_step": L * L,
-               "d2h_bytes_per_step": 8,
-               "path": "pgg_set_lattice(pinned host, L*L bytes) + pgg_step_mcs(1, host counts)"}
+        e2e = {"value": L * L * reps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8, "path": how + " + pgg_step_mcs(1, host counts)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -153,6 +153,14 @@ int pgg_get_lattice(pgg_ctx *ctx, uint8_t *host_out, uint64_t *step_out);
  * whole state). The seed is kept. Synchronises the stream. */
 int pgg_set_lattice(pgg_ctx *ctx, const uint8_t *host_in, uint64_t step);
 
+/* The same two transfers with the lattice bit-packed on the host: L rows of L/32 uint32 words,
+ * bit b of word w of a row = column 32w + b (1 = C), the device layout of PGG_BITPACK, so a
+ * checkpoint or an upload moves L*L/8 bytes instead of L*L. Need L % 32 == 0 (either layout;
+ * a PGG_U8 context converts on the device through its staging buffer). Synchronise the
+ * stream. */
+int pgg_get_lattice_packed(pgg_ctx *ctx, uint32_t *host_words_out, uint64_t *step_out);
+int pgg_set_lattice_packed(pgg_ctx *ctx, const uint32_t *host_words_in, uint64_t step);
+
 /* Current seed and step counter. */
 int pgg_get_state(const pgg_ctx *ctx, uint64_t *seed_out, uint64_t *step_out);
 

@@ -542,6 +542,48 @@ int pgg_set_lattice(pgg_ctx *c, const uint8_t *host_in, uint64_t step) {
     return PGG_OK;
 }
 
+int pgg_get_lattice_packed(pgg_ctx *c, uint32_t *host_words_out, uint64_t *step_out) {
+    g_last_error.clear();
+    if (!c || !host_words_out) return fail(PGG_ERR_ARG, "pgg_get_lattice_packed: NULL argument");
+    if (c->L % 32 != 0) return fail(PGG_ERR_ARG, "pgg_get_lattice_packed: needs L %% 32 == 0 (L = %d)", c->L);
+    PGG_CUDA(cudaSetDevice(c->device));
+    const size_t bytes = static_cast<size_t>(c->L) * c->L / 8;
+    if (c->layout == PGG_BITPACK) {
+        PGG_CUDA(cudaMemcpyAsync(host_words_out, c->lat, bytes, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        int rc = ensure_staging(c);
+        if (rc) return rc;
+        PGG_CUDA(pgg::launch_pack(static_cast<const uint8_t *>(c->lat), reinterpret_cast<uint32_t *>(c->staging_d), c->L,
+                                  c->stream));
+        PGG_CUDA(cudaMemcpyAsync(host_words_out, c->staging_d, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    if (step_out) *step_out = c->step;
+    return check_status(c);
+}
+
+int pgg_set_lattice_packed(pgg_ctx *c, const uint32_t *host_words_in, uint64_t step) {
+    g_last_error.clear();
+    if (!c || !host_words_in) return fail(PGG_ERR_ARG, "pgg_set_lattice_packed: NULL argument");
+    if (c->L % 32 != 0) return fail(PGG_ERR_ARG, "pgg_set_lattice_packed: needs L %% 32 == 0 (L = %d)", c->L);
+    if (step >= kMaxStep) return fail(PGG_ERR_ARG, "pgg_set_lattice_packed: step >= 2^56");
+    PGG_CUDA(cudaSetDevice(c->device));
+    const size_t bytes = static_cast<size_t>(c->L) * c->L / 8;
+    if (c->layout == PGG_BITPACK) {
+        PGG_CUDA(cudaMemcpyAsync(c->lat, host_words_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        int rc = ensure_staging(c);
+        if (rc) return rc;
+        PGG_CUDA(cudaMemcpyAsync(c->staging_d, host_words_in, bytes, cudaMemcpyHostToDevice, c->stream));
+        PGG_CUDA(pgg::launch_unpack(reinterpret_cast<const uint32_t *>(c->staging_d), static_cast<uint8_t *>(c->lat), c->L,
+                                    c->stream));
+    }
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    c->step = step;
+    c->running_valid = false;
+    return PGG_OK;
+}
+
 int pgg_get_state(const pgg_ctx *c, uint64_t *seed_out, uint64_t *step_out) {
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_get_state: NULL context");

@@ -53,6 +53,8 @@ def _declare(lib):
         "pgg_get_lattice": (ctypes.c_int, [_vp, _u8p, _u64p]),
         "pgg_set_lattice": (ctypes.c_int, [_vp, _u8p, ctypes.c_uint64]),
         "pgg_get_state": (ctypes.c_int, [_vp, _u64p, _u64p]),
+        "pgg_get_lattice_packed": (ctypes.c_int, [_vp, _u32p, _u64p]),
+        "pgg_set_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
         "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]),
         "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
@@ -234,6 +236,24 @@ class Lattice:
         """pgg_set_lattice from a raw host pointer (e.g. pinned memory)."""
         check(self.lib.pgg_set_lattice(self._h, ctypes.cast(host_ptr, _u8p), int(step)),
               "pgg_set_lattice")
+
+    def get_packed(self) -> tuple[np.ndarray, int]:
+        """pgg_get_lattice_packed: (L, L/32) uint32 words, bit b of word w = column 32w + b."""
+        out = np.empty((self.L, self.L // 32), dtype=np.uint32)
+        step = ctypes.c_uint64()
+        check(self.lib.pgg_get_lattice_packed(self._h, _ptr(out, _u32p), ctypes.byref(step)),
+              "pgg_get_lattice_packed")
+        return out, int(step.value)
+
+    def set_packed(self, words: np.ndarray, step: int = 0) -> None:
+        a = np.ascontiguousarray(words, dtype=np.uint32)
+        assert a.shape == (self.L, self.L // 32)
+        check(self.lib.pgg_set_lattice_packed(self._h, _ptr(a, _u32p), int(step)), "pgg_set_lattice_packed")
+
+    def set_packed_from_pointer(self, host_ptr: int, step: int = 0) -> None:
+        """pgg_set_lattice_packed from a raw host pointer (e.g. pinned memory)."""
+        check(self.lib.pgg_set_lattice_packed(self._h, ctypes.cast(host_ptr, _u32p), int(step)),
+              "pgg_set_lattice_packed")
 
     def state(self) -> tuple[int, int]:
         seed, step = ctypes.c_uint64(), ctypes.c_uint64()

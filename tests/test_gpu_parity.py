@@ -197,6 +197,31 @@ def test_checkpoint_resume_is_exact(pgg, layout):
     assert np.array_equal(ca, np.concatenate([c1, c2]))
 
 
+@pytest.mark.parametrize("layout", ["u8", "bitpack"])
+def test_packed_host_transfers(o, pgg, layout):
+    """pgg_get/set_lattice_packed carry the same state as the uint8 transfers (bit b of word
+    w = column 32w + b), and a run resumed from a packed checkpoint matches the oracle."""
+    L = 256
+    lat0 = inputs.random_lattice(L, 0.4, seed=21)
+    words = (lat0.reshape(L, L // 32, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(-1)
+    words = words.astype(np.uint32)
+    with pgg.Lattice(L, 3.9, 0.5, layout=layout) as lat:
+        lat.seed(5)
+        lat.set_packed(words, 16 * 7)
+        got, step = lat.get()
+        assert step == 16 * 7 and np.array_equal(got, lat0)
+        back, _ = lat.get_packed()
+        assert np.array_equal(back, words)
+        counts = lat.step_mcs(9)
+        final, _ = lat.get()
+        packed_final, _ = lat.get_packed()
+    ref = lat0.copy()
+    want = o.run(ref, 3.9, 0.5, 5, 16 * 7, 9, threads=THREADS)
+    assert np.array_equal(counts, want) and np.array_equal(final, ref)
+    bits = ((packed_final[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(L, L)
+    assert np.array_equal(bits.astype(np.uint8), ref)
+
+
 def test_layouts_and_schedules_agree_L1024(pgg):
     ref = None
     for layout in ("u8", "bitpack"):
