@@ -93,12 +93,13 @@ typedef enum {
                               memory, tile_x = words per thread (4 or 8), tile_y = threads
                               per block (64, 128 or 256); the cooperator count is carried as
                               a running total */
-    PGG_KERNEL_RESIDENT = 4 /* bit-packed lattices with L % 256 == 0 whose rows fit the SMs'
+    PGG_KERNEL_RESIDENT = 4 /* L % 256 == 0 with the bit-packed rows fitting the SMs'
                               shared memory: one cooperative launch per pgg_step_mcs call,
                               each CTA keeps a band of rows for all MCS and exchanges its 3
                               edge rows with its neighbours between sublattice steps; waits
                               are bounded (a time-out returns PGG_ERR_TIMEOUT at the next
-                              synchronising call) */
+                              synchronising call). A PGG_U8 lattice is packed into a scratch
+                              bit-packed copy at the start of the call and unpacked at its end */
 } pgg_kernel;
 
 /* Create a context for one L x L lattice with synergy factor r and noise K (Section III,

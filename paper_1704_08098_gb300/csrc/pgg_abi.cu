@@ -127,6 +127,7 @@ struct pgg_ctx {
     int sms = 0;
     size_t smem_optin = 0;
     uint32_t *mailbox_d = nullptr;
+    uint32_t *packed_d = nullptr;  // bit-packed copy of a uint8 lattice during a resident call
     unsigned int *ctr_d = nullptr;
     int *status_d = nullptr;
     unsigned int spin_limit = 1u << 22;
@@ -387,9 +388,19 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             if (e == cudaSuccess) e = cudaMalloc(&c->ctr_d, sizeof(unsigned int) * bands);
             if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(resident buffers): %s", cudaGetErrorString(e));
         }
+        // the kernel works on the bit-packed form: a uint8 lattice is packed for the call
+        uint32_t *packed = static_cast<uint32_t *>(c->lat);
+        if (c->layout == PGG_U8) {
+            if (!c->packed_d) {
+                cudaError_t e = cudaMalloc(&c->packed_d, static_cast<size_t>(c->L) * c->L / 8);
+                if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(packed copy): %s", cudaGetErrorString(e));
+            }
+            packed = c->packed_d;
+            PGG_CUDA(pgg::launch_pack(static_cast<const uint8_t *>(c->lat), packed, c->L, c->stream));
+        }
         pgg::ResidentArgs a;
         a.game = c->game;
-        a.lat = static_cast<uint32_t *>(c->lat);
+        a.lat = packed;
         a.L = c->L;
         a.n_bands = bands;
         a.seed = c->seed;
@@ -407,6 +418,8 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             PGG_CUDA(pgg::launch_resident(a, c->stream));
             c->step += 16ull * static_cast<uint64_t>(a.n_mcs);
         }
+        if (c->layout == PGG_U8)
+            PGG_CUDA(pgg::launch_unpack(packed, static_cast<uint8_t *>(c->lat), c->L, c->stream));
         c->running_valid = false;
         if (coop_per_mcs) {
             const size_t bytes = static_cast<size_t>(n_mcs) * sizeof(uint64_t);
@@ -600,7 +613,7 @@ int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, i
         return fail(PGG_ERR_ARG, "pgg_set_schedule: unknown kernel %d", kernel);
     if (kernel == PGG_KERNEL_RESIDENT) {
         if (pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) < 1)
-            return fail(PGG_ERR_ARG, "pgg_set_schedule: this lattice cannot be resident (bit-packed, L %% 256 == 0, rows within shared memory)");
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: this lattice cannot be resident (L %% 256 == 0, rows within shared memory)");
         c->kernel = kernel;
         c->k_fuse = 16;
         c->tile_x = 0;
@@ -772,6 +785,7 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->staging_d) cudaFree(c->staging_d);
     if (c->running_d) cudaFree(c->running_d);
     if (c->mailbox_d) cudaFree(c->mailbox_d);
+    if (c->packed_d) cudaFree(c->packed_d);
     if (c->ctr_d) cudaFree(c->ctr_d);
     if (c->status_d) cudaFree(c->status_d);
     delete c;

@@ -358,9 +358,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
 }  // namespace
 
 // Bands for a lattice of side L: one per SM when every band keeps at least 4 rows and its
-// rows fit the shared memory; 0 when the lattice cannot be resident.
+// rows fit the shared memory; 0 when the lattice cannot be resident. The kernel works on the
+// bit-packed form; a uint8 lattice is packed for the call by the caller.
 int resident_bands(int layout, int L, int sms, size_t smem_optin) {
-    if (layout != kPacked || L < 256 || L % 256 != 0 || sms < 1) return 0;
+    (void)layout;
+    if (L < 256 || L % 256 != 0 || sms < 1) return 0;
     int n = sms;
     while (n > 1 && L / n < 4) --n;
     const int max_rows = (L + n - 1) / n;

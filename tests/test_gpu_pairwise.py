@@ -126,10 +126,11 @@ def test_pair_direct_kernel(o, pgg, sched, L):
     assert np.array_equal(got_lat, want_lat)
 
 
+@pytest.mark.parametrize("layout", ["bitpack", "u8"])
 @pytest.mark.parametrize("L,n_mcs", [(256, 10), (1024, 6), (4096, 2)])
-def test_pair_resident_kernel(o, pgg, L, n_mcs):
+def test_pair_resident_kernel(o, pgg, L, n_mcs, layout):
     want_lat, want_counts = run_oracle(o, L, SNOWDRIFT, 0.5, 90 + L, n_mcs)
-    got_lat, got_counts, k = run_gpu(pgg, L, SNOWDRIFT, 0.5, 90 + L, n_mcs, "bitpack", dict(kernel="resident"))
+    got_lat, got_counts, k = run_gpu(pgg, L, SNOWDRIFT, 0.5, 90 + L, n_mcs, layout, dict(kernel="resident"))
     assert k == 16 * n_mcs
     assert np.array_equal(got_counts, want_counts)
     assert np.array_equal(got_lat, want_lat)

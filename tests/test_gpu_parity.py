@@ -307,7 +307,7 @@ def test_autotune_restores_state_and_keeps_results(o, pgg, layout, L):
         best = lat.autotune(1)
         after, k_after = lat.get()
         assert k_before == k_after and np.array_equal(before, after)
-        assert best["kernel"] in ("direct", "tiled", "simple") and best["ms_per_mcs"] > 0
+        assert best["kernel"] in ("resident", "direct", "tiled", "simple") and best["ms_per_mcs"] > 0
         counts = lat.step_mcs(6)
         final, _ = lat.get()
     ref = before.copy()
@@ -315,10 +315,12 @@ def test_autotune_restores_state_and_keeps_results(o, pgg, layout, L):
     assert np.array_equal(counts, want) and np.array_equal(final, ref)
 
 
+@pytest.mark.parametrize("layout", ["bitpack", "u8"])
 @pytest.mark.parametrize("L,n_mcs", [(256, 12), (768, 6), (1024, 8), (4096, 2)])
-def test_resident_kernel(o, pgg, L, n_mcs):
+def test_resident_kernel(o, pgg, L, n_mcs, layout):
+    """Both layouts (a uint8 lattice runs on a packed copy for the call)."""
     want_lat, want_counts = run_oracle(o, L, 3.8, 0.5, 60 + L, n_mcs)
-    got_lat, got_counts, k = run_gpu(pgg, L, 3.8, 0.5, 60 + L, n_mcs, "bitpack", dict(kernel="resident"))
+    got_lat, got_counts, k = run_gpu(pgg, L, 3.8, 0.5, 60 + L, n_mcs, layout, dict(kernel="resident"))
     assert k == 16 * n_mcs
     assert np.array_equal(got_counts, want_counts)
     assert np.array_equal(got_lat, want_lat)
