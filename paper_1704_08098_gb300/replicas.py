@@ -28,7 +28,8 @@ def make_workload(n: int, seed: int = 7):
 
 
 def run(n: int = 512, n_mcs: int = 5000, chunk: int = 500, tune_mcs: int = 20,
-        per_replica_sample: int = 16, per_replica_mcs: int = 50, seed: int = 7) -> dict:
+        per_replica_sample: int = 16, per_replica_mcs: int = 50, seed: int = 7,
+        autotune: bool = True, compare: bool = True) -> dict:
     import torch
     from . import build, pgg
     build.build()
@@ -38,7 +39,7 @@ def run(n: int = 512, n_mcs: int = 5000, chunk: int = 500, tune_mcs: int = 20,
     out = {"n": n, "n_mcs": n_mcs, "sizes": {int(x): int((L == x).sum()) for x in np.unique(L)}}
     with pgg.Batch(L, r, 0.5, seeds, stream=stream.cuda_stream) as b:
         b.seed(0.5)
-        out["autotune"] = b.autotune(tune_mcs)
+        out["autotune"] = b.autotune(tune_mcs) if autotune else None
         torch.cuda.synchronize()
         counts = np.zeros((n, n_mcs), dtype=np.uint32)
         dev = torch.zeros((n, chunk), dtype=torch.int32, device="cuda")
@@ -60,6 +61,8 @@ def run(n: int = 512, n_mcs: int = 5000, chunk: int = 500, tune_mcs: int = 20,
                       "site_updates_per_s": sites_per_mcs * n_mcs / (gpu_ms / 1e3)}
     out["final_rho"] = {"mean": float((counts[:, -1] / L.astype(np.float64) ** 2).mean()),
                         "absorbed": int((counts[:, -1] == 0).sum())}
+    if not compare:
+        return out
     # one launch sequence per replica (the single-lattice API), on a sample of replicas
     idx = np.random.default_rng(seed).choice(n, size=min(per_replica_sample, n), replace=False)
     per_ms = 0.0
@@ -88,8 +91,11 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--mcs", type=int, default=5000)
     ap.add_argument("--chunk", type=int, default=500)
+    ap.add_argument("--no-autotune", action="store_true", help="library default CTA size and team warps")
+    ap.add_argument("--no-compare", action="store_true", help="skip the one-launch-sequence-per-replica timing")
     args = ap.parse_args()
-    print(json.dumps(run(args.n, args.mcs, args.chunk)))
+    print(json.dumps(run(args.n, args.mcs, args.chunk, autotune=not args.no_autotune,
+                         compare=not args.no_compare)))
 
 
 if __name__ == "__main__":
