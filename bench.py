@@ -424,17 +424,12 @@ def main():
 
     # end to end through the public API with host buffers: upload the lattice from pinned
     # memory, run one MCS, read the count back
-    # (bit-packed lattices travel in their packed form, L*L/8 bytes)
+    # (the lattice travels in its bit-packed host form, L*L/8 bytes, for either device layout)
     e2e = None
     if not args.no_e2e:
-        if args.layout == "bitpack":
-            host_words, _ = lat.get_packed()
-            pinned = torch.from_numpy(host_words.reshape(-1).view(np.int32)).pin_memory()
-            upload, h2d, how = lat.set_packed_from_pointer, L * L // 8, "pgg_set_lattice_packed(pinned host, L*L/8 bytes)"
-        else:
-            host_lat, _ = lat.get()
-            pinned = torch.from_numpy(host_lat.reshape(-1)).pin_memory()
-            upload, h2d, how = lat.set_from_pointer, L * L, "pgg_set_lattice(pinned host, L*L bytes)"
+        host_words, _ = lat.get_packed()
+        pinned = torch.from_numpy(host_words.reshape(-1).view(np.int32)).pin_memory()
+        upload, h2d, how = lat.set_packed_from_pointer, L * L // 8, "pgg_set_lattice_packed(pinned host, L*L/8 bytes)"
         counts = np.zeros(1, dtype=np.uint64)
         reps = max(3, min(args.steps, 10))
         torch.cuda.synchronize()

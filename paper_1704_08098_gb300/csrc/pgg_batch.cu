@@ -47,6 +47,18 @@ struct ReplicaDesc {
     PhiloxKeys rk;
 };
 
+// Initial condition of every replica in one launch: blockIdx.y strides over the replicas,
+// the x blocks over the words of one replica (smaller replicas leave blocks idle).
+__global__ void k_batch_init(const ReplicaDesc *__restrict__ desc, int n, uint64_t thr) {
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
+        const ReplicaDesc d = desc[i];
+        const uint64_t n_words = static_cast<uint64_t>(d.L) * d.L / 32;
+        for (uint64_t wi = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; wi < n_words;
+             wi += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+            d.lat[wi] = init_packed_word(wi, d.seed, thr);
+    }
+}
+
 struct Job {
     int first;       // index into members[]
     int n_teams;     // replicas in the job
@@ -433,11 +445,18 @@ int pgg_batch_seed(pgg_batch *b, double p) {
     if (!(p >= 0.0 && p <= 1.0)) return bfail(PGG_ERR_ARG, "pgg_batch_seed: p must be in [0, 1]");
     PGG_BCUDA(cudaSetDevice(b->device));
     const uint64_t thr = p >= 1.0 ? (1ull << 32) : static_cast<uint64_t>(p * 4294967296.0);
+    int max_L = 0;
     for (int i = 0; i < b->n; ++i) {
-        PGG_BCUDA(pgg::launch_init(pgg::kPacked, b->host_desc[i].lat, b->L[i], b->seeds[i], thr, b->stream));
         b->host_desc[i].step = 0;
+        max_L = std::max(max_L, b->L[i]);
     }
     PGG_BCUDA(cudaMemcpyAsync(b->desc_d, b->host_desc.data(), size_t(b->n) * sizeof(ReplicaDesc), cudaMemcpyHostToDevice, b->stream));
+    // one launch for all replicas, from the descriptors just uploaded
+    const uint64_t max_words = static_cast<uint64_t>(max_L) * max_L / 32;
+    const unsigned gx = static_cast<unsigned>(std::min<uint64_t>((max_words + 255) / 256, 1024));
+    const unsigned gy = static_cast<unsigned>(std::min(b->n, 65535));
+    pgg::k_batch_init<<<dim3(gx, gy), 256, 0, b->stream>>>(b->desc_d, b->n, thr);
+    PGG_BCUDA(cudaGetLastError());
     PGG_BCUDA(cudaStreamSynchronize(b->stream));
     return PGG_OK;
 }

@@ -130,4 +130,21 @@ __device__ __forceinline__ int wrap_near(int v, int L) {
     return v < 0 ? v + L : (v >= L ? v - L : v);
 }
 
+// Initial condition (Section III) of bit-packed word wi (sites 32 wi .. 32 wi + 31, row-major
+// index): one Philox call per 4 sites, site C iff its word is below thr = floor(p 2^32).
+__device__ __forceinline__ uint32_t init_packed_word(uint64_t wi, uint64_t seed, uint64_t thr) {
+    uint32_t bits = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint64_t q = wi * 8 + c;
+        const uint4 w = philox4x32_10(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32), 0u, kTagInit,
+                                      static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+        bits |= (static_cast<uint32_t>(static_cast<uint64_t>(w.x) < thr) << (4 * c + 0)) |
+                (static_cast<uint32_t>(static_cast<uint64_t>(w.y) < thr) << (4 * c + 1)) |
+                (static_cast<uint32_t>(static_cast<uint64_t>(w.z) < thr) << (4 * c + 2)) |
+                (static_cast<uint32_t>(static_cast<uint64_t>(w.w) < thr) << (4 * c + 3));
+    }
+    return bits;
+}
+
 }  // namespace pgg

@@ -38,21 +38,8 @@ __global__ void k_init_u8(uint8_t *__restrict__ lat, uint64_t n_quads, uint64_t 
 __global__ void k_init_packed(uint32_t *__restrict__ lat, uint64_t n_words, uint64_t seed,
                               uint64_t thr) {
     for (uint64_t wi = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; wi < n_words;
-         wi += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t bits = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint64_t q = wi * 8 + c;
-            const uint4 w = philox4x32_10(static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32),
-                                          0u, kTagInit, static_cast<uint32_t>(seed),
-                                          static_cast<uint32_t>(seed >> 32));
-            bits |= (static_cast<uint32_t>(static_cast<uint64_t>(w.x) < thr) << (4 * c + 0)) |
-                    (static_cast<uint32_t>(static_cast<uint64_t>(w.y) < thr) << (4 * c + 1)) |
-                    (static_cast<uint32_t>(static_cast<uint64_t>(w.z) < thr) << (4 * c + 2)) |
-                    (static_cast<uint32_t>(static_cast<uint64_t>(w.w) < thr) << (4 * c + 3));
-        }
-        lat[wi] = bits;
-    }
+         wi += (uint64_t)gridDim.x * blockDim.x)
+        lat[wi] = init_packed_word(wi, seed, thr);
 }
 
 // ---------------------------------------------------------------------------------
