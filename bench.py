@@ -39,8 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 NCU = {
     "direct:386f968aaf80d09d:bitpack:8192:1:4:64": {"alu_warp_inst": 4870544, "dram_bytes": 8450560},
-    "resident:5478c475fbb154d9:bitpack:8192:16:152:0": {"alu_warp_inst": 74880849, "dram_bytes": 8488192},
-    "resident-pairwise:5478c475fbb154d9:bitpack:8192:16:152:0": {"alu_warp_inst": 61368478, "dram_bytes": 8478720},
+    "resident:68d01c0081670dc5:bitpack:8192:16:152:0": {"alu_warp_inst": 74880712, "dram_bytes": 8488192},
+    "resident-pairwise:68d01c0081670dc5:bitpack:8192:16:152:0": {"alu_warp_inst": 61368942, "dram_bytes": 8478976},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
