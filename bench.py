@@ -40,6 +40,8 @@ FALLBACK_HBM_GBS = 6800.0
 NCU = {
     "direct:386f968aaf80d09d:bitpack:8192:1:4:64": {"alu_warp_inst": 4870544, "dram_bytes": 8450560},
     "resident:68d01c0081670dc5:bitpack:8192:16:152:0": {"alu_warp_inst": 74880712, "dram_bytes": 8488192},
+    # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
+    "resident:68d01c0081670dc5:u8:8192:16:152:0": {"alu_warp_inst": 74880712, "dram_bytes": 8488192},
     "resident-pairwise:68d01c0081670dc5:bitpack:8192:16:152:0": {"alu_warp_inst": 61368942, "dram_bytes": 8478976},
 }
 

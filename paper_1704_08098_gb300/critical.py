@@ -10,6 +10,7 @@ recovers above r_c, so near r_c the late-time density is stationary only for tim
 beyond the critical relaxation time; the fit is as good as the run is long.
 
     python -m paper_1704_08098_gb300.critical --L 8192 --T 100000
+    python -m paper_1704_08098_gb300.critical --L 4096 --T 100000 --r-lo 3.75 --r-hi 3.90 --r-step 0.01
 """
 from __future__ import annotations
 
@@ -115,8 +116,12 @@ def main():
     ap.add_argument("--T", type=int, default=100000)
     ap.add_argument("--layout", default="bitpack")
     ap.add_argument("--chunk", type=int, default=500)
+    ap.add_argument("--r-lo", type=float, default=3.730)
+    ap.add_argument("--r-hi", type=float, default=3.760)
+    ap.add_argument("--r-step", type=float, default=0.002)
     args = ap.parse_args()
-    res = sweep(args.L, T=args.T, layout=args.layout, chunk=args.chunk)
+    r_values = np.round(np.arange(args.r_lo, args.r_hi + 0.5 * args.r_step, args.r_step), 6)
+    res = sweep(args.L, r_values=r_values, T=args.T, layout=args.layout, chunk=args.chunk)
     res["analysis"] = analyse(res)
     print(json.dumps(res))
 
