@@ -81,7 +81,10 @@ typedef enum {
 
 /* Kernel family used by pgg_step_mcs. */
 typedef enum {
-    PGG_KERNEL_AUTO = 0,   /* the tuned default for (L, layout) */
+    PGG_KERNEL_AUTO = 0,   /* the schedule pgg_autotune chose for (device, L, layout, game);
+                              before any tuning: the resident kernel for L >= 2048 where it
+                              fits, else the direct kernel (bit-packed, L % 256 == 0), else
+                              the tiled kernel (L % 64 == 0), else the simple one */
     PGG_KERNEL_SIMPLE = 1, /* one launch per sublattice step, one thread per 8 sites,
                               operands from global memory; the plain baseline */
     PGG_KERNEL_TILED = 2,  /* shared-memory tiles with a 3k-site halo (2k for the pairwise

@@ -159,7 +159,9 @@ Schedule resolve_schedule(const pgg_ctx *c) {
     Schedule s{c->kernel, c->k_fuse, c->tile_x, c->tile_y};
     if (s.kernel == PGG_KERNEL_AUTO) tuned_lookup(c, &s);  // then resolved like an explicit choice
     if (s.kernel == PGG_KERNEL_AUTO) {
-        if (pgg::direct_supported(c->layout, c->L)) {
+        if (c->L >= 2048 && pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) > 0) {
+            s = {PGG_KERNEL_RESIDENT, 16, 0, 0};
+        } else if (pgg::direct_supported(c->layout, c->L)) {
             s = {PGG_KERNEL_DIRECT, 1, 8, 256};
         } else if (!tiled_supported(c)) {
             s = {PGG_KERNEL_SIMPLE, 1, 0, 0};
