@@ -193,6 +193,15 @@ __device__ __forceinline__ void bulk_commit_and_wait() {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
+// 4-byte global -> shared copy in the thread's cp.async group, and the wait for all of them
+__device__ __forceinline__ void copy_async4(uint32_t *dst, const uint32_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
@@ -225,17 +234,19 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         if (tid == 0) atomicExch(p.status, 2);
         return;
     }
-    for (int t = tid; t < kTableEntries; t += kResThreads) s_table[t] = p.table[t];
+    for (int t = tid; t < kTableEntries; t += kResThreads) copy_async4(&s_table[t], &p.table[t]);
     if (tid == 0) {
         s_abort = 0;
         mbar_init(&s_mbar, 1);
     }
-    // stage band + halo (rows r0 - 3 .. r0 + nb + 2, periodic)
+    // stage the table and band + halo (rows r0 - 3 .. r0 + nb + 2, periodic) with 4-byte
+    // asynchronous copies (cp.async: many loads in flight per thread, each word to its place)
     for (int x = tid; x < (nb + 6) * Lw; x += kResThreads) {
         const int lr = x / Lw, w = x - lr * Lw;
         const int g = wrap_small(r0 - 3 + lr, L);
-        s_rows[lr * Lw + swz(w)] = p.lat[static_cast<size_t>(g) * Lw + w];
+        copy_async4(&s_rows[lr * Lw + swz(w)], &p.lat[static_cast<size_t>(g) * Lw + w]);
     }
+    copy_async_wait_all();
     fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
     __syncthreads();
     uint4 ocall = make_uint4(0, 0, 0, 0);
