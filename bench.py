@@ -392,6 +392,10 @@ def main():
     # MCS time / launches (includes launch gaps, so it understates the kernel's own rate)
     k = sched["steps_per_launch"]
     launches_per_mcs = 16 // k
+    # other kernels of ours per MCS: the pack and unpack around a resident call on a uint8
+    # lattice, the count of the simple kernel
+    extra_launches_per_mcs = (2 if sched["kernel"] == "resident" and args.layout == "u8" else 0) + \
+        (1 if sched["kernel"] == "simple" else 0)
     launch_s = (total_ms / args.steps) / launches_per_mcs / 1e3
     updates_per_launch = L * L / 16.0 * k
     pk, pk_kind = peaks()
@@ -462,7 +466,7 @@ def main():
                                               "excluded by the per-step CUDA events)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches_per_mcs * args.steps,
+        "gpu_launches": (launches_per_mcs + extra_launches_per_mcs) * args.steps,
         "clocks": clocks, "wall_s": wall, "step_ms": step_ms,
     }
     if rank == 0:
