@@ -339,6 +339,21 @@ def test_resident_full_size_and_resume(o, pgg):
     assert np.array_equal(got, want_lat)
 
 
+def test_resident_largest_lattice_and_beyond(o, pgg):
+    """The largest side whose bands still fit the shared memory (L = 14336: 94-95 rows of
+    448 words per CTA) against the oracle; one side more that cannot be resident is refused
+    (the direct kernel remains available for it)."""
+    L = 14336
+    want_lat, want_counts = run_oracle(o, L, 3.8, 0.5, 8, 1)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 3.8, 0.5, 8, 1, "bitpack", dict(kernel="resident"))
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+    with pgg.Lattice(16384, 3.8, 0.5, layout="bitpack") as lat:
+        with pytest.raises(pgg.PGGError):
+            lat.set_schedule("resident")
+        assert lat.schedule()["kernel"] == "direct"
+
+
 def test_resident_wait_timeout_is_reported(o, pgg):
     """A bounded wait that runs out (spin limit 0: every wait gives up at once) returns
     PGG_ERR_TIMEOUT at the next synchronising call; the context stays usable."""
