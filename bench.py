@@ -263,8 +263,9 @@ def algorithmic_bytes_per_update(layout: str, k: int) -> float:
 
 
 def cpu_baseline(args, budget_s=12.0):
-    """The CPU oracle, as it stands, on this host's cores: one MCS on the same workload
-    (more if it finishes early), timed with a steady clock."""
+    """The CPU oracle, as it stands, on this host's cores: whole MCS of the same workload
+    until about budget_s seconds of CPU work (at least one MCS, at most 32), timed with a
+    steady clock."""
     import oracle
     o = oracle.Oracle()
     threads = os.cpu_count() or 1
@@ -276,7 +277,7 @@ def cpu_baseline(args, budget_s=12.0):
         oracle_mcs(o, lat, args, 16 * n, threads)
         n += 1
         el = time.perf_counter() - t0
-        if el > budget_s / 2 or n >= 8:
+        if el * (n + 1) / n > budget_s or n >= 32:
             break
     return {"value": L * L * n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} MCS of the L={L} workload from its Bernoulli(0.5) start "
