@@ -354,6 +354,16 @@ def test_resident_largest_lattice_and_beyond(o, pgg):
         assert lat.schedule()["kernel"] == "direct"
 
 
+@pytest.mark.parametrize("L", [16384, 32768])
+def test_beyond_resident_sizes_default_schedule(o, pgg, L):
+    """Lattices too large to be resident, up to the largest side the ABI accepts (32768:
+    1.07e9 sites), in the default schedule (the direct kernel), one MCS against the oracle."""
+    want_lat, want_counts = run_oracle(o, L, 3.9, 0.5, 3, 1)
+    got_lat, got_counts, _ = run_gpu(pgg, L, 3.9, 0.5, 3, 1, "bitpack")
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
 def test_resident_wait_timeout_is_reported(o, pgg):
     """A bounded wait that runs out (spin limit 0: every wait gives up at once) returns
     PGG_ERR_TIMEOUT at the next synchronising call; the context stays usable."""
