@@ -39,10 +39,10 @@ FALLBACK_HBM_GBS = 6800.0
 # dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 NCU = {
     "direct:386f968aaf80d09d:bitpack:8192:1:4:64": {"alu_warp_inst": 4870544, "dram_bytes": 8450560},
-    "resident:57fb716087385467:bitpack:8192:16:152:0": {"alu_warp_inst": 74879537, "dram_bytes": 8492032},
+    "resident:68b7428b492d0191:bitpack:8192:16:152:0": {"alu_warp_inst": 74879328, "dram_bytes": 8488448},
     # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
-    "resident:57fb716087385467:u8:8192:16:152:0": {"alu_warp_inst": 74879537, "dram_bytes": 8492032},
-    "resident-pairwise:57fb716087385467:bitpack:8192:16:152:0": {"alu_warp_inst": 61367740, "dram_bytes": 8479232},
+    "resident:68b7428b492d0191:u8:8192:16:152:0": {"alu_warp_inst": 74879328, "dram_bytes": 8488448},
+    "resident-pairwise:68b7428b492d0191:bitpack:8192:16:152:0": {"alu_warp_inst": 61367096, "dram_bytes": 8479232},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).

@@ -232,7 +232,10 @@ int check_status(pgg_ctx *c) {
         PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
         PGG_CUDA(cudaStreamSynchronize(c->stream));
         c->running_valid = false;
-        if (st == 2)
+        if (st & 4)
+            return fail(PGG_ERR_STATE, "an index check of the checked build failed: a kernel computed an address "
+                                       "outside its buffer (the access was skipped; the lattice is not a valid state)");
+        if (st & 2)
             return fail(PGG_ERR_CUDA, "the resident kernel found its shared rows or the mailbox not 16-byte aligned "
                                       "and did not run; the lattice is unchanged");
         return fail(PGG_ERR_TIMEOUT,
@@ -454,7 +457,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         if (s.kernel == PGG_KERNEL_DIRECT) {
             for (int j = 0; j < 16; ++j) {
                 PGG_CUDA(pgg::launch_step_direct(c->game, static_cast<uint32_t *>(c->lat), c->L, c->seed, c->step, c->table_d,
-                                                 c->running_d, s.tile_x, s.tile_y, c->stream));
+                                                 c->running_d, c->status_d, s.tile_x, s.tile_y, c->stream));
                 ++c->step;
             }
             PGG_CUDA(cudaMemcpyAsync(c->counts_d + m, c->running_d, sizeof(unsigned long long),
@@ -480,6 +483,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
                 a.tile_y = s.tile_y;
                 a.table = c->table_d;
                 a.count_out = (j + s.k == 16) ? c->counts_d + m : nullptr;
+                a.status = c->status_d;
                 PGG_CUDA(pgg::launch_step_tiled(a, c->stream));
                 if (s.k > 1) {
                     void *t = c->lat;

@@ -147,4 +147,27 @@ __device__ __forceinline__ uint32_t init_packed_word(uint64_t wi, uint64_t seed,
     return bits;
 }
 
+// Checked build (compiled with -DPGG_CHECKED=1, a separate library used by the tests): every
+// shared- and global-memory index of the step kernels is tested against its buffer before the
+// access; a failed test sets bit 2 (value 4) of the context's status word and skips the access,
+// so the host reports it at the next synchronising call. In the normal build the test is the
+// constant true and costs nothing.
+#ifndef PGG_CHECKED
+#define PGG_CHECKED 0
+#endif
+constexpr int kStatusIndexCheck = 4;
+
+__device__ __forceinline__ bool index_ok(long long idx, long long n, int *status) {
+#if PGG_CHECKED
+    if (idx >= 0 && idx < n) return true;
+    if (status) atomicOr(status, kStatusIndexCheck);
+    return false;
+#else
+    (void)idx;
+    (void)n;
+    (void)status;
+    return true;
+#endif
+}
+
 }  // namespace pgg

@@ -58,6 +58,7 @@ struct TiledArgs {
     int tile_y;  // sites, multiple of 4
     const uint32_t *table;
     unsigned long long *count_out;
+    int *status;  // | 4 when an index check fails (checked build); nullable
 };
 cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s);
 
@@ -66,7 +67,7 @@ cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s);
 // *running (if not NULL) += the change in the number of cooperators. Needs L % 256 == 0.
 bool direct_supported(int layout, int L);
 cudaError_t launch_step_direct(int game, uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
-                               unsigned long long *running, int upt, int block, cudaStream_t s);
+                               unsigned long long *running, int *status, int upt, int block, cudaStream_t s);
 // Shared memory (bytes) the tiled kernel needs for a configuration; 0 if unsupported.
 size_t tiled_smem_bytes(int layout, int game, int steps, int tile_x, int tile_y);
 
@@ -83,7 +84,8 @@ struct ResidentArgs {
     uint32_t *mailbox;            // resident_mailbox_words(L, n_bands) words
     unsigned int *ctr;            // n_bands counters
     unsigned long long *counts;   // n_mcs counts, zeroed by the caller
-    int *status;                  // set to 1 if a bounded wait ran out, 2 if the alignment check failed
+    int *status;                  // | 1 a bounded wait ran out, | 2 the alignment check failed, | 4 an index
+                                  // check failed (checked build)
     unsigned int spin_limit;      // polls before a wait gives up
 };
 int resident_bands(int layout, int L, int sms, size_t smem_optin);

@@ -37,6 +37,7 @@ struct DirectParams {
     int n_tasks;           // (L / 4) * tasks_per_row
     const uint32_t *table;
     unsigned long long *running;  // cooperator count, += this step's change (nullable)
+    int *status;                  // | 4 when an index check fails (checked build)
     PhiloxKeys rk;
 };
 
@@ -46,6 +47,7 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
     long long delta = 0;
     const uint32_t kl = static_cast<uint32_t>(p.k), kh = static_cast<uint32_t>(p.k >> 32) | kTagDir;
     const int stride = gridDim.x * blockDim.x;
+    const long long n_words = static_cast<long long>(p.L) * p.Lw;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < p.n_tasks; t += stride) {
         const int a = p.task_magic ? static_cast<int>(__umulhi(static_cast<uint32_t>(t), p.task_magic)) : t;
         const int w0 = (t - a * p.tasks_per_row) * UPT;
@@ -59,8 +61,8 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            wl[q] = reads_row<GAME>(q) ? p.lat[rowoff[q] + wprev] : 0u;
-            wc[q] = reads_row<GAME>(q) ? p.lat[rowoff[q] + w0] : 0u;
+            wl[q] = reads_row<GAME>(q) && index_ok(rowoff[q] + wprev, n_words, p.status) ? p.lat[rowoff[q] + wprev] : 0u;
+            wc[q] = reads_row<GAME>(q) && index_ok(rowoff[q] + w0, n_words, p.status) ? p.lat[rowoff[q] + w0] : 0u;
         }
         const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(a), kl, kh), rk);
         UnitCtx u;
@@ -73,12 +75,13 @@ __device__ __forceinline__ long long direct_body(const DirectParams &p, const Ph
             const int w = w0 + s;
             const int wn = w + 1 == p.Lw ? 0 : w + 1;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) wr[q] = reads_row<GAME>(q) ? p.lat[rowoff[q] + wn] : 0u;
+            for (int q = 0; q < 7; ++q)
+                wr[q] = reads_row<GAME>(q) && index_ok(rowoff[q] + wn, n_words, p.status) ? p.lat[rowoff[q] + wn] : 0u;
             u.gw = w;
             u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
             uint32_t sx;
             const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
-            if (flips) {
+            if (flips && index_ok(rowoff[3] + w, n_words, p.status)) {
                 p.lat[rowoff[3] + w] = wc[3] ^ (flips << OJ);
                 delta += __popc(flips & ~sx) - __popc(flips & sx);
             }
@@ -161,7 +164,7 @@ cudaError_t launch_direct_game(const DirectParams &p, int upt, int block, cudaSt
 bool direct_supported(int layout, int L) { return layout == kPacked && L >= 256 && L % 256 == 0; }
 
 cudaError_t launch_step_direct(int game, uint32_t *lat, int L, uint64_t seed, uint64_t k, const uint32_t *table,
-                               unsigned long long *running, int upt, int block, cudaStream_t s) {
+                               unsigned long long *running, int *status, int upt, int block, cudaStream_t s) {
     if (L < 256 || L % 256 != 0 || (upt != 4 && upt != 8)) return cudaErrorInvalidValue;
     DirectParams p;
     p.lat = lat;
@@ -175,6 +178,7 @@ cudaError_t launch_step_direct(int game, uint32_t *lat, int L, uint64_t seed, ui
     p.n_tasks = (L / 4) * p.tasks_per_row;
     p.table = table;
     p.running = running;
+    p.status = status;
     p.rk = philox_round_keys(seed);
     return game == kPairGame ? launch_direct_game<kPairGame>(p, upt, block, s)
                              : launch_direct_game<kGroupGame>(p, upt, block, s);

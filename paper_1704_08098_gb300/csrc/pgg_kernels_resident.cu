@@ -47,7 +47,7 @@ struct ResidentParams {
     uint32_t *mailbox;        // [band][parity][top/bottom][3 rows][Lw]
     unsigned int *ctr;        // [band] completed steps
     unsigned long long *counts;  // [n_mcs], zeroed before the launch
-    int *status;              // set to 1 on a wait time-out
+    int *status;              // 1: a wait timed out; | 4: an index check failed (checked build)
     unsigned int spin_limit;
     PhiloxKeys rk;
 };
@@ -99,8 +99,9 @@ __device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
 // side, so the two calls touch disjoint sites and need no barrier between them.
 template <int OJ, int GAME>
 __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *__restrict__ s_table,
-                                              const PhiloxKeys &rk, int Lw, int r0, const BandRows &br,
-                                              bool edge, uint64_t k) {
+                                              const PhiloxKeys &rk, int Lw, int r0, int nb, const BandRows &br,
+                                              bool edge, uint64_t k, int *status) {
+    const long long n_local = static_cast<long long>(nb + 6) * Lw;  // words of band + halo
     // edge: selected row q is 0 or n_srows - 1 (edge_top: whether row 0 is one of them)
     const bool edge_top = br.in_lo != 0, edge_bot = br.in_hi < br.n_srows;
     const int n_rows_sel = edge ? static_cast<int>(edge_top) + static_cast<int>(edge_bot) : br.in_hi - br.in_lo;
@@ -123,8 +124,9 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            wl[q] = reads_row<GAME>(q) ? row0[q * Lw + swz(wprev)] : 0u;
-            wc[q] = reads_row<GAME>(q) ? row0[q * Lw + swz(w0)] : 0u;
+            const long long base = static_cast<long long>(lr - 3 + q) * Lw;
+            wl[q] = reads_row<GAME>(q) && index_ok(base + swz(wprev), n_local, status) ? row0[q * Lw + swz(wprev)] : 0u;
+            wc[q] = reads_row<GAME>(q) && index_ok(base + swz(w0), n_local, status) ? row0[q * Lw + swz(w0)] : 0u;
         }
         const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(i >> 2), kl, kh), rk);
         UnitCtx u;
@@ -135,12 +137,16 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
         for (int w = w0; w < w0 + upt; ++w) {
             const int wn = w + 1 == Lw ? 0 : w + 1;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) wr[q] = reads_row<GAME>(q) ? row0[q * Lw + swz(wn)] : 0u;
+            for (int q = 0; q < 7; ++q)
+                wr[q] = reads_row<GAME>(q) && index_ok(static_cast<long long>(lr - 3 + q) * Lw + swz(wn), n_local, status)
+                            ? row0[q * Lw + swz(wn)]
+                            : 0u;
             u.gw = w;
             u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
             uint32_t sx;
             const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
-            if (flips) s_rows[lr * Lw + swz(w)] = wc[3] ^ (flips << OJ);
+            // writes stay in the band's own rows (local rows 3 .. nb + 2)
+            if (flips && index_ok(lr - 3, nb, status)) s_rows[lr * Lw + swz(w)] = wc[3] ^ (flips << OJ);
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
                 wl[q] = wc[q];
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const PhiloxKeys rk = p.rk;
     // bulk copies need 16-byte aligned rows (the same answer in every CTA: all stop together)
     if ((smem_u32(s_rows) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u) {
-        if (tid == 0) atomicExch(p.status, 2);
+        if (tid == 0) atomicOr(p.status, 2);
         return;
     }
     for (int t = tid; t < kTableEntries; t += kResThreads) copy_async4(&s_table[t], &p.table[t]);
@@ -244,7 +250,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     for (int x = tid; x < (nb + 6) * Lw; x += kResThreads) {
         const int lr = x / Lw, w = x - lr * Lw;
         const int g = wrap_small(r0 - 3 + lr, L);
-        copy_async4(&s_rows[lr * Lw + swz(w)], &p.lat[static_cast<size_t>(g) * Lw + w]);
+        if (index_ok(static_cast<long long>(g) * Lw + w, static_cast<long long>(L) * Lw, p.status))
+            copy_async4(&s_rows[lr * Lw + swz(w)], &p.lat[static_cast<size_t>(g) * Lw + w]);
     }
     copy_async_wait_all();
     fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                     ++it;
                 }
                 if (it >= p.spin_limit) {
-                    atomicExch(p.status, 1);
+                    atomicOr(p.status, 1);
                     s_abort = 1;
                 } else {
                     const int par = (j - 1) & 1;
@@ -289,10 +296,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
             const BandRows br = band_rows<GAME>(r0, nb, o >> 2);
             // interior rows read only the band's own rows: they run while the halo is in flight
             switch (o & 3) {
-                case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-                case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-                case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
-                default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, false, k); break;
+                case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
+                case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
+                case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
+                default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
             }
             bool ready = true;
             if (j > 0) {
@@ -307,10 +314,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
             if (ready) {
                 // the at most two edge rows, which read the halo
                 switch (o & 3) {
-                    case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-                    case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-                    case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
-                    default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, br, true, k); break;
+                    case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
+                    case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
+                    case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
+                    default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
                 }
             } else {
                 s_abort = 1;
@@ -362,7 +369,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     // store the band
     for (int x = tid; x < nb * Lw; x += kResThreads) {
         const int lr = x / Lw, w = x - lr * Lw;
-        p.lat[static_cast<size_t>(r0 + lr) * Lw + w] = s_rows[(lr + 3) * Lw + swz(w)];
+        if (index_ok(static_cast<long long>(r0 + lr) * Lw + w, static_cast<long long>(L) * Lw, p.status))
+            p.lat[static_cast<size_t>(r0 + lr) * Lw + w] = s_rows[(lr + 3) * Lw + swz(w)];
     }
 }
 

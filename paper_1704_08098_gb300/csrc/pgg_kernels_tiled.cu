@@ -45,6 +45,8 @@ struct TiledParams {
     int dir_words;  // uint32 words reserved for the two direction buffers
     const uint32_t *table;
     unsigned long long *count_out;
+    int *status;           // | 4 when an index check fails (checked build); nullable
+    long long tile_words;  // words of the shared tile buffer (Wr * RP for a full tile)
     PhiloxKeys rk;  // round keys of the seed
 };
 
@@ -160,13 +162,15 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, const PhiloxKeys
         const int w = g.w_lo + (t - sr * g.n_words);
         const int r = g.r_first + 4 * sr;
         uint32_t *col = s_tile + w * RP + r;
+        const long long ci = static_cast<long long>(w) * RP + r;  // index of col[0] in the tile
         uint32_t wl[7], wc[7], wr[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
             // rows r-3 .. r+3; a game reads only rows r-R .. r+R, all inside the staged tile
-            wl[q] = reads_row<GAME>(q) ? col[q - 3 - RP] : 0u;
-            wc[q] = reads_row<GAME>(q) ? col[q - 3] : 0u;
-            wr[q] = reads_row<GAME>(q) ? col[q - 3 + RP] : 0u;
+            const bool rq = reads_row<GAME>(q);
+            wl[q] = rq && index_ok(ci + q - 3 - RP, p.tile_words, p.status) ? col[q - 3 - RP] : 0u;
+            wc[q] = rq && index_ok(ci + q - 3, p.tile_words, p.status) ? col[q - 3] : 0u;
+            wr[q] = rq && index_ok(ci + q - 3 + RP, p.tile_words, p.status) ? col[q - 3 + RP] : 0u;
         }
         const int U = x0w - p.hw + w;
         const int grow = wrap_small(y0 - p.H + r, p.L);
@@ -183,18 +187,21 @@ __device__ __forceinline__ void tile_step(const TiledParams &p, const PhiloxKeys
         }
         uint32_t sx;
         const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
-        if (flips) {
+        if (flips && index_ok(ci, p.tile_words, p.status)) {
             const uint32_t nw = wc[3] ^ (flips << OJ);
             col[0] = nw;
             if (in_place) {
                 if (LAYOUT == kPacked) {
-                    static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + u.gw] = nw;
+                    if (index_ok(static_cast<long long>(grow) * p.Lw + u.gw, static_cast<long long>(p.L) * p.Lw, p.status))
+                        static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + u.gw] = nw;
                 } else {
                     uint8_t *rowp = static_cast<uint8_t *>(p.dst) + static_cast<size_t>(grow) * p.L + 32 * u.gw + OJ;
                     const uint32_t newbits = (sx ^ flips);
 #pragma unroll
                     for (int m = 0; m < 8; ++m)
-                        if (flips & (1u << (4 * m))) rowp[4 * m] = static_cast<uint8_t>((newbits >> (4 * m)) & 1u);
+                        if ((flips & (1u << (4 * m))) &&
+                            index_ok(static_cast<long long>(grow) * p.L + 32 * u.gw + OJ + 4 * m, static_cast<long long>(p.L) * p.L, p.status))
+                            rowp[4 * m] = static_cast<uint8_t>((newbits >> (4 * m)) & 1u);
                 }
             }
         }
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(cons
                                                                        static_cast<size_t>(grow) * p.L + 32 * gw);
                     bits = pack32(src[0], src[1]);
                 }
-                s_tile[w * RP + r] = bits;
+                if (index_ok(static_cast<long long>(w) * RP + r, p.tile_words, p.status)) s_tile[w * RP + r] = bits;
                 gw = wrap_small(gw + 32, p.Lw);
             }
         }
@@ -272,12 +279,15 @@ __global__ void __launch_bounds__(BLOCK, PGG_TILED_MIN_BLOCKS) k_step_tiled(cons
         const int iwords = iw >> 5;
         for (int rr = warp; rr < ih; rr += kWarps) {
             for (int ww = lane; ww < iwords; ww += 32) {
-                const uint32_t bits = s_tile[(p.hw + ww) * RP + p.H + rr];
+                const long long ti = static_cast<long long>(p.hw + ww) * RP + p.H + rr;
+                const uint32_t bits = index_ok(ti, p.tile_words, p.status) ? s_tile[ti] : 0u;
                 cnt += __popc(bits);
                 if (p.steps > 1) {
                     const int grow = y0 + rr;
                     const int gw = x0w + ww;
-                    if (LAYOUT == kPacked) {
+                    // the word's 32 sites, as one packed word or 32 bytes
+                    if (!index_ok(static_cast<long long>(grow) * p.Lw + gw, static_cast<long long>(p.L) * p.Lw, p.status)) {
+                    } else if (LAYOUT == kPacked) {
                         static_cast<uint32_t *>(p.dst)[static_cast<size_t>(grow) * p.Lw + gw] = bits;
                     } else {
                         uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.dst) +
@@ -386,6 +396,8 @@ cudaError_t launch_step_tiled(const TiledArgs &a, cudaStream_t s) {
     p.RP = column_pitch(a.steps, p.R, a.tile_y);
     p.table = a.table;
     p.count_out = a.count_out;
+    p.status = a.status;
+    p.tile_words = static_cast<long long>(a.tile_x / 32 + 2 * p.hw) * p.RP;
     p.rk = philox_round_keys(a.seed);
     const size_t smem = smem_bytes_for(a.steps, p.R, a.tile_x, a.tile_y, &p.dir_slot, &p.dir_words);
     if (smem > kMaxSmem) return cudaErrorInvalidValue;

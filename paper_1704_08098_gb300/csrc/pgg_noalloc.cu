@@ -103,6 +103,7 @@ extern "C" int pgg_step_mcs_noalloc(const void *lattice_in, void *lattice_out, i
         for (int half = 0; half < 16 / kFuse; ++half) {
             pgg::TiledArgs a;
             a.game = pgg::kGroupGame;
+            a.status = nullptr;
             a.src = src;
             a.dst = half == 0 ? static_cast<void *>(scratch) : lattice_out;
             a.L = L;

@@ -14,6 +14,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libpgg.so")
+LIB_CHECKED_PATH = os.path.join(_PKG, "_lib", "libpgg_checked.so")
 
 PGG_OK, PGG_ERR_ARG, PGG_ERR_CUDA, PGG_ERR_OOM, PGG_ERR_TIMEOUT, PGG_ERR_STATE = 0, -1, -2, -3, -4, -5
 U8, BITPACK = 0, 1
@@ -26,6 +27,7 @@ KERNELS = {"auto": KERNEL_AUTO, "simple": KERNEL_SIMPLE, "tiled": KERNEL_TILED, 
            "resident": KERNEL_RESIDENT}
 
 _lib = None
+_lib_checked = None
 
 _vp = ctypes.c_void_p
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -101,28 +103,36 @@ def _declare(lib):
     return lib
 
 
-def load():
-    """Load libpgg.so (raises if it was not built)."""
-    global _lib
-    if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing; "
+def load(checked: bool = False):
+    """Load libpgg.so, or with checked=True the index-checking build libpgg_checked.so
+    (raises if it was not built)."""
+    global _lib, _lib_checked
+    if (_lib_checked if checked else _lib) is None:
+        path = LIB_CHECKED_PATH if checked else LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing; "
                                "run paper_1704_08098_gb300.build.build()")
         try:  # let the library share PyTorch's CUDA runtime when torch is present
             import torch  # noqa: F401
         except Exception:
             pass
-        _lib = _declare(ctypes.CDLL(LIB_PATH))
-    return _lib
+        lib = _declare(ctypes.CDLL(path))
+        if checked:
+            _lib_checked = lib
+        else:
+            _lib = lib
+    return _lib_checked if checked else _lib
 
 
-def last_error() -> str:
-    return load().pgg_last_error().decode()
+def last_error(lib=None) -> str:
+    return (lib or load()).pgg_last_error().decode()
 
 
-def check(status: int, where: str) -> None:
+def check(status: int, where: str, lib=None) -> None:
+    """Raise PGGError with the library's last message when status is not PGG_OK (lib: the
+    library that made the call, the normal build by default)."""
     if status != PGG_OK:
-        raise PGGError(status, where, last_error())
+        raise PGGError(status, where, last_error(lib))
 
 
 def current_stream_handle() -> int:
@@ -143,15 +153,20 @@ def _ptr(a: np.ndarray, t):
 class Lattice:
     """One L x L lattice context (``pgg_ctx``)."""
 
-    def __init__(self, L: int, r: float, K: float, layout="u8", stream: int | None = None):
-        self.lib = load()
+    def __init__(self, L: int, r: float, K: float, layout="u8", stream: int | None = None,
+                 checked: bool = False):
+        """checked=True runs on the index-checking build of the library (tests)."""
+        self.lib = load(checked)
         self.L = int(L)
         self.layout = LAYOUTS[layout]
         self.stream = current_stream_handle() if stream is None else int(stream)
         h = _vp()
-        check(self.lib.pgg_create(ctypes.byref(h), self.L, float(r), float(K), self.layout,
+        self._check(self.lib.pgg_create(ctypes.byref(h), self.L, float(r), float(K), self.layout,
                                   _vp(self.stream)), "pgg_create")
         self._h = h
+
+    def _check(self, status: int, where: str) -> None:
+        check(status, where, self.lib)
 
     # -- lifetime ------------------------------------------------------------
     def close(self) -> None:
@@ -173,7 +188,7 @@ class Lattice:
 
     # -- ABI calls -------------------------------------------------------------
     def set_params(self, r: float, K: float) -> None:
-        check(self.lib.pgg_set_params(self._h, float(r), float(K)), "pgg_set_params")
+        self._check(self.lib.pgg_set_params(self._h, float(r), float(K)), "pgg_set_params")
 
     def set_game(self, game="group", payoff=None) -> None:
         """pgg_set_game: "group" (the default) or "pairwise" with payoff = (R, S, T, P)."""
@@ -184,17 +199,17 @@ class Lattice:
             pay = np.ascontiguousarray(np.asarray(payoff, dtype=np.float64))
             assert pay.shape == (4,)
             ptr = pay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        check(self.lib.pgg_set_game(self._h, g, ptr), "pgg_set_game")
+        self._check(self.lib.pgg_set_game(self._h, g, ptr), "pgg_set_game")
 
     def game(self) -> tuple[str, tuple]:
         g = ctypes.c_int()
         pay = np.zeros(4, dtype=np.float64)
-        check(self.lib.pgg_get_game(self._h, ctypes.byref(g),
+        self._check(self.lib.pgg_get_game(self._h, ctypes.byref(g),
                                     pay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "pgg_get_game")
         return ("pairwise" if g.value == GAME_PAIRWISE else "group"), tuple(float(x) for x in pay)
 
     def seed(self, seed: int, p: float = 0.5) -> None:
-        check(self.lib.pgg_seed(self._h, int(seed), float(p)), "pgg_seed")
+        self._check(self.lib.pgg_seed(self._h, int(seed), float(p)), "pgg_seed")
 
     def step_mcs(self, n_mcs: int, counts: np.ndarray | int | None = None):
         """Advance n_mcs MCS. ``counts`` may be None (no counts), a host uint64 numpy
@@ -202,77 +217,77 @@ class Lattice:
         pointer (filled asynchronously). With counts=None a host array is returned."""
         if counts is None:
             out = np.zeros(max(int(n_mcs), 1), dtype=np.uint64)
-            check(self.lib.pgg_step_mcs(self._h, int(n_mcs), out.ctypes.data), "pgg_step_mcs")
+            self._check(self.lib.pgg_step_mcs(self._h, int(n_mcs), out.ctypes.data), "pgg_step_mcs")
             return out[:n_mcs]
         if isinstance(counts, np.ndarray):
             assert counts.dtype == np.uint64 and counts.size >= n_mcs and counts.flags.c_contiguous
-            check(self.lib.pgg_step_mcs(self._h, int(n_mcs), counts.ctypes.data), "pgg_step_mcs")
+            self._check(self.lib.pgg_step_mcs(self._h, int(n_mcs), counts.ctypes.data), "pgg_step_mcs")
             return counts
-        check(self.lib.pgg_step_mcs(self._h, int(n_mcs), _vp(int(counts))), "pgg_step_mcs")
+        self._check(self.lib.pgg_step_mcs(self._h, int(n_mcs), _vp(int(counts))), "pgg_step_mcs")
         return None
 
     def advance(self, n_mcs: int) -> None:
         """Advance n_mcs MCS without reading counts (asynchronous)."""
-        check(self.lib.pgg_step_mcs(self._h, int(n_mcs), None), "pgg_step_mcs")
+        self._check(self.lib.pgg_step_mcs(self._h, int(n_mcs), None), "pgg_step_mcs")
 
     def count(self) -> int:
         v = ctypes.c_uint64()
-        check(self.lib.pgg_count_coop(self._h, ctypes.byref(v)), "pgg_count_coop")
+        self._check(self.lib.pgg_count_coop(self._h, ctypes.byref(v)), "pgg_count_coop")
         return int(v.value)
 
     def get(self) -> tuple[np.ndarray, int]:
         out = np.empty((self.L, self.L), dtype=np.uint8)
         step = ctypes.c_uint64()
-        check(self.lib.pgg_get_lattice(self._h, _ptr(out, _u8p), ctypes.byref(step)),
+        self._check(self.lib.pgg_get_lattice(self._h, _ptr(out, _u8p), ctypes.byref(step)),
               "pgg_get_lattice")
         return out, int(step.value)
 
     def set(self, lattice: np.ndarray, step: int = 0) -> None:
         a = np.ascontiguousarray(lattice, dtype=np.uint8)
         assert a.shape == (self.L, self.L)
-        check(self.lib.pgg_set_lattice(self._h, _ptr(a, _u8p), int(step)), "pgg_set_lattice")
+        self._check(self.lib.pgg_set_lattice(self._h, _ptr(a, _u8p), int(step)), "pgg_set_lattice")
 
     def set_from_pointer(self, host_ptr: int, step: int = 0) -> None:
         """pgg_set_lattice from a raw host pointer (e.g. pinned memory)."""
-        check(self.lib.pgg_set_lattice(self._h, ctypes.cast(host_ptr, _u8p), int(step)),
+        self._check(self.lib.pgg_set_lattice(self._h, ctypes.cast(host_ptr, _u8p), int(step)),
               "pgg_set_lattice")
 
     def get_packed(self) -> tuple[np.ndarray, int]:
         """pgg_get_lattice_packed: (L, L/32) uint32 words, bit b of word w = column 32w + b."""
         out = np.empty((self.L, self.L // 32), dtype=np.uint32)
         step = ctypes.c_uint64()
-        check(self.lib.pgg_get_lattice_packed(self._h, _ptr(out, _u32p), ctypes.byref(step)),
+        self._check(self.lib.pgg_get_lattice_packed(self._h, _ptr(out, _u32p), ctypes.byref(step)),
               "pgg_get_lattice_packed")
         return out, int(step.value)
 
     def set_packed(self, words: np.ndarray, step: int = 0) -> None:
         a = np.ascontiguousarray(words, dtype=np.uint32)
         assert a.shape == (self.L, self.L // 32)
-        check(self.lib.pgg_set_lattice_packed(self._h, _ptr(a, _u32p), int(step)), "pgg_set_lattice_packed")
+        self._check(self.lib.pgg_set_lattice_packed(self._h, _ptr(a, _u32p), int(step)), "pgg_set_lattice_packed")
 
     def set_packed_from_pointer(self, host_ptr: int, step: int = 0) -> None:
         """pgg_set_lattice_packed from a raw host pointer (e.g. pinned memory)."""
-        check(self.lib.pgg_set_lattice_packed(self._h, ctypes.cast(host_ptr, _u32p), int(step)),
+        self._check(self.lib.pgg_set_lattice_packed(self._h, ctypes.cast(host_ptr, _u32p), int(step)),
               "pgg_set_lattice_packed")
 
     def state(self) -> tuple[int, int]:
         seed, step = ctypes.c_uint64(), ctypes.c_uint64()
-        check(self.lib.pgg_get_state(self._h, ctypes.byref(seed), ctypes.byref(step)),
+        self._check(self.lib.pgg_get_state(self._h, ctypes.byref(seed), ctypes.byref(step)),
               "pgg_get_state")
         return int(seed.value), int(step.value)
 
     def set_schedule(self, kernel="auto", steps_per_launch: int = 1, tile_x: int = 0,
                      tile_y: int = 0) -> None:
         kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-        check(self.lib.pgg_set_schedule(self._h, kern, int(steps_per_launch), int(tile_x),
+        self._check(self.lib.pgg_set_schedule(self._h, kern, int(steps_per_launch), int(tile_x),
                                         int(tile_y)), "pgg_set_schedule")
 
     def set_spin_limit(self, limit: int) -> None:
-        check(self.lib.pgg_set_spin_limit(self._h, int(limit)), "pgg_set_spin_limit")
+        self._check(self.lib.pgg_set_spin_limit(self._h, int(limit)), "pgg_set_spin_limit")
 
     def schedule(self) -> dict:
         v = [ctypes.c_int() for _ in range(4)]
-        check(self.lib.pgg_get_schedule(self._h, *[ctypes.byref(x) for x in v]),
+        self._check(self.lib.pgg_get_schedule(self._h, *[ctypes.byref(x) for x in v]),
               "pgg_get_schedule")
         names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_AUTO: "auto", KERNEL_DIRECT: "direct",
                  KERNEL_RESIDENT: "resident"}
@@ -283,7 +298,7 @@ class Lattice:
         """pgg_autotune: pick the fastest schedule for this (device, L, layout)."""
         v = [ctypes.c_int() for _ in range(4)]
         ms = ctypes.c_float()
-        check(self.lib.pgg_autotune(self._h, int(n_mcs), *[ctypes.byref(x) for x in v],
+        self._check(self.lib.pgg_autotune(self._h, int(n_mcs), *[ctypes.byref(x) for x in v],
                                     ctypes.byref(ms)), "pgg_autotune")
         names = {KERNEL_SIMPLE: "simple", KERNEL_TILED: "tiled", KERNEL_DIRECT: "direct",
                  KERNEL_RESIDENT: "resident"}
@@ -292,13 +307,13 @@ class Lattice:
 
     def threshold_table(self) -> np.ndarray:
         out = np.zeros(2 * 26 * 26, dtype=np.uint32)
-        check(self.lib.pgg_get_threshold_table(self._h, _ptr(out, _u32p)),
+        self._check(self.lib.pgg_get_threshold_table(self._h, _ptr(out, _u32p)),
               "pgg_get_threshold_table")
         return out.reshape(2, 26, 26)
 
     def device_ptr(self) -> tuple[int, int]:
         p, n = _vp(), ctypes.c_uint64()
-        check(self.lib.pgg_lattice_device_ptr(self._h, ctypes.byref(p), ctypes.byref(n)),
+        self._check(self.lib.pgg_lattice_device_ptr(self._h, ctypes.byref(p), ctypes.byref(n)),
               "pgg_lattice_device_ptr")
         return int(p.value or 0), int(n.value)
 
