@@ -11,6 +11,7 @@ beyond the critical relaxation time; the fit is as good as the run is long.
 
     python -m paper_1704_08098_gb300.critical --L 8192 --T 100000
     python -m paper_1704_08098_gb300.critical --L 4096 --T 100000 --r-lo 3.75 --r-hi 3.90 --r-step 0.01
+    python -m paper_1704_08098_gb300.critical --anneal --L 2048 --T 100000 --r-lo 3.748 --r-hi 3.800 --r-step 0.004
 """
 from __future__ import annotations
 
@@ -110,6 +111,67 @@ def analyse(res: dict, t_min_frac: float = 0.01, late_frac: float = 0.3,
             "paper": {"r_c": 3.7443, "beta": 0.56, "beta_dp": 0.584}}
 
 
+def anneal_scan(L: int = 2048, r_values=None, T_relax: int = 100000, T_meas: int = 100000,
+                seed: int = 1, K: float = 0.5, chunk: int = 5000, layout: str = "bitpack") -> dict:
+    """Stationary cooperator density by annealing (Section V's procedure for the stationary
+    state): one lattice, started from Bernoulli(1/2) at the largest r, is carried down the r
+    values in decreasing order; at each r it relaxes for T_relax MCS (discarded) and is then
+    averaged over T_meas MCS. Starting each r from the state of the previous one avoids the
+    collapse-and-recovery transient of a random start."""
+    import torch
+    from . import build, pgg
+    build.build()
+    if r_values is None:
+        r_values = np.round(np.arange(3.800, 3.7479, -0.004), 6)
+    r_values = np.sort(np.asarray(r_values, dtype=np.float64))[::-1]
+    stream = torch.cuda.current_stream()
+    counts = torch.zeros(chunk, dtype=torch.int64, device="cuda")
+    N = float(L) * L
+    out = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with pgg.Lattice(L, float(r_values[0]), K, layout=layout, stream=stream.cuda_stream) as lat:
+        lat.seed(seed, 0.5)
+        if L >= 1024:
+            lat.autotune(2)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for r in r_values:
+            lat.set_params(float(r), K)
+            lat.advance(T_relax)
+            total, sq, done, last = 0.0, 0.0, 0, 0
+            while done < T_meas:
+                m = min(chunk, T_meas - done)
+                lat.step_mcs(m, counts.data_ptr())
+                c = counts[:m].double() / N
+                total += float(c.sum())
+                sq += float((c * c).sum())
+                last = float(c[-1])
+                done += m
+            mean = total / T_meas
+            out.append({"r": float(r), "rho": mean, "rho_std": float(np.sqrt(max(sq / T_meas - mean * mean, 0.0))),
+                        "rho_end": last, "absorbed": last == 0.0})
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    res = {"L": L, "K": K, "T_relax": T_relax, "T_meas": T_meas, "seed": seed, "points": out,
+           "gpu_s": ev0.elapsed_time(ev1) / 1e3}
+    # fit rho = A (r - r_c)^beta over the surviving points, with r_c free and with the paper's r_c
+    rs = np.array([p["r"] for p in out if p["rho"] > 0])
+    ys = np.log(np.array([p["rho"] for p in out if p["rho"] > 0]))
+    if len(rs) >= 3:
+        best = None
+        for rc in np.arange(rs.min() - 0.02, rs.min() - 1e-5, 1e-5):
+            X = np.log(rs - rc)
+            beta, logA = np.polyfit(X, ys, 1)
+            resid = float(np.sum((ys - (beta * X + logA)) ** 2))
+            if best is None or resid < best[0]:
+                best = (resid, rc, beta)
+        beta_paper_rc = float(np.polyfit(np.log(rs - 3.7443), ys, 1)[0]) if rs.min() > 3.7443 else None
+        res["fit"] = {"r_c": float(best[1]), "beta": float(best[2]), "residual": best[0],
+                      "beta_with_paper_r_c": beta_paper_rc, "points": int(len(rs))}
+    res["paper"] = {"r_c": 3.7443, "beta": 0.56}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L", type=int, default=8192)
@@ -119,8 +181,13 @@ def main():
     ap.add_argument("--r-lo", type=float, default=3.730)
     ap.add_argument("--r-hi", type=float, default=3.760)
     ap.add_argument("--r-step", type=float, default=0.002)
+    ap.add_argument("--anneal", action="store_true",
+                    help="stationary densities by annealing down in r (T relaxation + T averaging per r)")
     args = ap.parse_args()
     r_values = np.round(np.arange(args.r_lo, args.r_hi + 0.5 * args.r_step, args.r_step), 6)
+    if args.anneal:
+        print(json.dumps(anneal_scan(args.L, r_values, T_relax=args.T, T_meas=args.T, layout=args.layout)))
+        return
     res = sweep(args.L, r_values=r_values, T=args.T, layout=args.layout, chunk=args.chunk)
     res["analysis"] = analyse(res)
     print(json.dumps(res))
