@@ -94,21 +94,32 @@ def analyse(res: dict, t_min_frac: float = 0.01, late_frac: float = 0.3,
         late[i] = float(np.nanmean(rho[i, lw]))
         per_r.append({"r": float(r[i]), "late_slope": slope, "rho_late": late[i],
                       "rho_T": float(rho[i, -1])})
-    fit = None
     use = late > rho_floor
-    if use.sum() >= 3:
-        rs, ys = r[use], np.log(late[use])
-        best = None
-        for rc in np.arange(rs.min() - 0.03, rs.min() - 1e-5, 1e-5):
-            X = np.log(rs - rc)
-            beta, logA = np.polyfit(X, ys, 1)
-            resid = float(np.sum((ys - (beta * X + logA)) ** 2))
-            if best is None or resid < best[0]:
-                best = (resid, rc, beta, logA)
-        fit = {"r_c": float(best[1]), "beta": float(best[2]), "A": float(np.exp(best[3])),
-               "residual": best[0], "points": int(use.sum())}
+    fit = fit_power_law(r[use], late[use], window=0.03)
     return {"per_r": per_r, "power_law_fit": fit,
             "paper": {"r_c": 3.7443, "beta": 0.56, "beta_dp": 0.584}}
+
+
+def fit_power_law(r, rho, window: float = 0.02, r_c_fixed: float = 3.7443):
+    """Least-squares fit of log rho = beta log(r - r_c) + log A (Eq. (5)) over points with
+    rho > 0: r_c scanned in steps of 1e-5 over the `window` below the smallest r; also beta
+    with r_c fixed at the paper's value. None with fewer than 3 points."""
+    r = np.asarray(r, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.float64)
+    ok = rho > 0
+    if ok.sum() < 3:
+        return None
+    rs, ys = r[ok], np.log(rho[ok])
+    best = None
+    for rc in np.arange(rs.min() - window, rs.min() - 1e-5, 1e-5):
+        X = np.log(rs - rc)
+        beta, logA = np.polyfit(X, ys, 1)
+        resid = float(np.sum((ys - (beta * X + logA)) ** 2))
+        if best is None or resid < best[0]:
+            best = (resid, rc, beta, logA)
+    fixed = float(np.polyfit(np.log(rs - r_c_fixed), ys, 1)[0]) if rs.min() > r_c_fixed else None
+    return {"r_c": float(best[1]), "beta": float(best[2]), "A": float(np.exp(best[3])), "residual": best[0],
+            "points": int(ok.sum()), "beta_with_paper_r_c": fixed}
 
 
 def anneal_scan(L: int = 2048, r_values=None, T_relax: int = 100000, T_meas: int = 100000,
@@ -155,19 +166,7 @@ def anneal_scan(L: int = 2048, r_values=None, T_relax: int = 100000, T_meas: int
     res = {"L": L, "K": K, "T_relax": T_relax, "T_meas": T_meas, "seed": seed, "points": out,
            "gpu_s": ev0.elapsed_time(ev1) / 1e3}
     # fit rho = A (r - r_c)^beta over the surviving points, with r_c free and with the paper's r_c
-    rs = np.array([p["r"] for p in out if p["rho"] > 0])
-    ys = np.log(np.array([p["rho"] for p in out if p["rho"] > 0]))
-    if len(rs) >= 3:
-        best = None
-        for rc in np.arange(rs.min() - 0.02, rs.min() - 1e-5, 1e-5):
-            X = np.log(rs - rc)
-            beta, logA = np.polyfit(X, ys, 1)
-            resid = float(np.sum((ys - (beta * X + logA)) ** 2))
-            if best is None or resid < best[0]:
-                best = (resid, rc, beta)
-        beta_paper_rc = float(np.polyfit(np.log(rs - 3.7443), ys, 1)[0]) if rs.min() > 3.7443 else None
-        res["fit"] = {"r_c": float(best[1]), "beta": float(best[2]), "residual": best[0],
-                      "beta_with_paper_r_c": beta_paper_rc, "points": int(len(rs))}
+    res["fit"] = fit_power_law([p["r"] for p in out], [p["rho"] for p in out])
     res["paper"] = {"r_c": 3.7443, "beta": 0.56}
     return res
 

@@ -25,3 +25,12 @@ def test_log_times_are_log_spaced_and_unique():
     assert t[0] == 1 and t[-1] == 100000
     assert np.all(np.diff(t) > 0)
     assert len(t) <= 101
+
+
+def test_direct_fit_recovers_known_exponent_and_fixed_rc_slope():
+    r = np.round(np.arange(3.748, 3.8001, 0.004), 6)
+    rho = 1.3 * (r - 3.7443) ** 0.58
+    fit = critical.fit_power_law(r, rho)
+    assert abs(fit["r_c"] - 3.7443) < 2e-4 and abs(fit["beta"] - 0.58) < 0.01
+    assert abs(fit["beta_with_paper_r_c"] - 0.58) < 1e-9
+    assert critical.fit_power_law(r[:2], rho[:2]) is None
