@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # only while that source is unchanged. alu_warp_inst = ALU-pipe warp instructions,
 # dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 NCU = {
-    "direct:386f968aaf80d09d:bitpack:8192:1:4:64": {"alu_warp_inst": 4870544, "dram_bytes": 8450560},
+    "direct:43120e8fff9f45cb:bitpack:8192:1:4:64": {"alu_warp_inst": 4876624, "dram_bytes": 8450560},
     "resident:68b7428b492d0191:bitpack:8192:16:152:0": {"alu_warp_inst": 74879328, "dram_bytes": 8488448},
     # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
     "resident:68b7428b492d0191:u8:8192:16:152:0": {"alu_warp_inst": 74879328, "dram_bytes": 8488448},
