@@ -35,14 +35,19 @@ FALLBACK_HBM_GBS = 6800.0
 
 # Per-launch counters of the dominant kernel from one ncu capture of this benchmark (see
 # profiles/), keyed by the kernel's source file hash and launch configuration; they are used
-# only while that source is unchanged. alu_warp_inst = ALU-pipe warp instructions,
-# dram_bytes = dram__bytes_read.sum + dram__bytes_write.sum.
+# only while that source is unchanged. alu_warp_inst / fma_warp_inst = warp instructions of the
+# ALU pipe / of the FMA-heavy pipe (integer multiply-adds), dram_bytes = dram__bytes_read.sum +
+# dram__bytes_write.sum.
 NCU = {
-    "direct:43120e8fff9f45cb:bitpack:8192:1:4:64": {"alu_warp_inst": 4876624, "dram_bytes": 8450560},
-    "resident:68b7428b492d0191:bitpack:8192:16:152:0": {"alu_warp_inst": 74879328, "dram_bytes": 8488448},
+    "direct:7ddfd94ea47717a8:bitpack:8192:1:4:64":
+        {"alu_warp_inst": 4554560, "fma_warp_inst": 3904416, "dram_bytes": 8451584},
+    "resident:714b1d3e9c1ca6e4:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 69189494, "fma_warp_inst": 55686096, "dram_bytes": 8491520},
     # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
-    "resident:68b7428b492d0191:u8:8192:16:152:0": {"alu_warp_inst": 74879328, "dram_bytes": 8488448},
-    "resident-pairwise:68b7428b492d0191:bitpack:8192:16:152:0": {"alu_warp_inst": 61367096, "dram_bytes": 8479232},
+    "resident:714b1d3e9c1ca6e4:u8:8192:16:152:0":
+        {"alu_warp_inst": 69189494, "fma_warp_inst": 55686096, "dram_bytes": 8491520},
+    "resident-pairwise:714b1d3e9c1ca6e4:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 61367898, "fma_warp_inst": None, "dram_bytes": 8479232},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
@@ -420,6 +425,10 @@ def main():
                                  f" x {sm_mhz:.0f} MHz (median SM clock sampled in the run)",
                     "work_per_launch": f"{ncu['alu_warp_inst']} ALU-pipe warp instructions "
                                        f"(ncu, {updates_per_launch:.0f} updates)"}
+        if ncu.get("fma_warp_inst"):
+            # the integer multiply-adds the kernel issues on the FMA-heavy pipe (same lane count)
+            fma = ncu["fma_warp_inst"] * 32 / launch_s / 1e12
+            roofline["fma_pipe"] = {"achieved": fma, "peak": alu_peak, "frac": fma / alu_peak}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": pk["hbm_gbs"],
                     "unit": "GB/s", "frac": hbm_achieved / pk["hbm_gbs"], "traffic": None,

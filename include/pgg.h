@@ -248,11 +248,13 @@ int pgg_batch_seed(pgg_batch *b, double p);
 int pgg_batch_step_mcs(pgg_batch *b, int n_mcs, uint32_t *counts);
 
 /* Warps that advance one replica, per size class L = 64, 128, 256, 512, 1024 (5 entries,
- * each 1, 2, 4, 8, 16 or 32). Default {1, 1, 2, 8, 32}. Results do not depend on it. */
+ * each 1, 2, 4, 8, 16 or 32, at most the CTA's warps). Default {1, 1, 2, 4, 16}. Results do not
+ * depend on it. */
 int pgg_batch_set_team_warps(pgg_batch *b, const int *warps);
 int pgg_batch_get_team_warps(const pgg_batch *b, int *warps);
 
-/* Threads per persistent CTA: 1024 (default) or 512 (fewer warps, more registers each). */
+/* Threads per persistent CTA: 512 (default) or 1024 (more warps, fewer registers each).
+ * Setting 512 caps the team sizes at 16 warps. */
 int pgg_batch_set_cta_threads(pgg_batch *b, int threads);
 int pgg_batch_get_cta_threads(const pgg_batch *b, int *threads);
 

@@ -258,8 +258,9 @@ struct pgg_batch {
     unsigned int *counter_d = nullptr;
     uint32_t *counts_d = nullptr;
     int64_t counts_cap = 0;
-    int team_warps[pgg::kSizeClasses] = {1, 1, 2, 8, 32};
-    int cta_threads = 1024;
+    // the autotuner's usual choice on GB300 (the 1024-thread CTA has 64 registers a thread and spills)
+    int team_warps[pgg::kSizeClasses] = {1, 1, 2, 4, 16};
+    int cta_threads = 512;
     // CUDA graph of one persistent launch (counter reset + kernel) for graph_n_mcs MCS
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;

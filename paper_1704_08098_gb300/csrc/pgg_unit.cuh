@@ -44,6 +44,12 @@ __device__ __forceinline__ uint32_t nibble_range(int m_lo, int m_hi) {
     return hi & lo;
 }
 
+// An opaque 1 in constant memory: x * c_one + y compiles to an integer multiply-add, issued on
+// the FMA pipe, where x + y would go to the ALU pipe. The group-count sums below use it for two of
+// their four additions, which balances the two pipes (the ALU pipe is otherwise the busier one:
+// 72 M against 43 M warp instructions per MCS at L = 8192 before, 67 M against 54 M after).
+static __constant__ uint32_t c_one = 1u;
+
 struct UnitCtx {
     uint64_t k;
     uint32_t a;       // sublattice row index of the unit
@@ -74,7 +80,7 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     if (!active) return 0u;
 
     // group counts n(di, dj) of the groups centred within distance 2 of the sites
-#define PGG_N(DI, DJ) (PGG_Y(DI, DJ) + PGG_Y(DI, (DJ) - 1) + PGG_Y(DI, (DJ) + 1) + PGG_Y((DI) - 1, DJ) + PGG_Y((DI) + 1, DJ))
+#define PGG_N(DI, DJ) (PGG_Y(DI, DJ) + PGG_Y(DI, (DJ) - 1) + (PGG_Y(DI, (DJ) + 1) * c_one + (PGG_Y((DI) - 1, DJ) * c_one + PGG_Y((DI) + 1, DJ))))
     const uint32_t n00 = PGG_N(0, 0), n0e = PGG_N(0, 1), n0w = PGG_N(0, -1);
     const uint32_t n0ee = PGG_N(0, 2), n0ww = PGG_N(0, -2);
     const uint32_t ns0 = PGG_N(1, 0), nn0 = PGG_N(-1, 0);
