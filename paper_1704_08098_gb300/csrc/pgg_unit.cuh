@@ -109,18 +109,14 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     const uint32_t Io01 = __byte_perm(Ao, 0u, 0x4140) * 26u + __byte_perm(Bo, 0u, 0x4140);  // m = 1, 3
     const uint32_t Io23 = __byte_perm(Ao, 0u, 0x4342) * 26u + __byte_perm(Bo, 0u, 0x4342);  // m = 5, 7
 
-    // adoption draws: call 2gw serves sites 0..3, call 2gw+1 sites 4..7 (only if needed)
+    // adoption draws: call 2gw serves sites 0..3, call 2gw+1 sites 4..7. Both calls run
+    // (interleaved) whenever the word has an active site: the lanes of a warp seldom need the
+    // same halves, and one uniform path costs the warp two calls where per-lane choices cost
+    // three (the divergent one-call and two-call paths one after the other)
     const uint32_t g0 = 2u * static_cast<uint32_t>(u.gw);
     const uint32_t kl = static_cast<uint32_t>(u.k), kh = static_cast<uint32_t>(u.k >> 32) | kTagU;
     uint4 u0 = make_uint4(g0, u.a, kl, kh), u1 = make_uint4(g0 + 1u, u.a, kl, kh);
-    const bool need0 = (active & 0x0000FFFFu) != 0, need1 = (active & 0xFFFF0000u) != 0;
-    if (need0 && need1) {
-        philox_rk2(u0, u1, rk);
-    } else {
-        // one call: a single inlined copy of the generator for either half
-        const uint4 r = philox_rk(need0 ? u0 : u1, rk);
-        if (need0) u0 = r; else u1 = r;
-    }
+    philox_rk2(u0, u1, rk);
 
     uint32_t flips = 0;
 #define PGG_SITE(M, IREG, HALF, UW)                                                 \
@@ -181,16 +177,11 @@ __device__ __forceinline__ uint32_t unit_flips_pair(const uint32_t (&wl)[7], con
     const uint32_t Ie = 25u * (sx & 0x01010101u) + 5u * (nx & kLowNib) + (ny & kLowNib);
     const uint32_t Io = 25u * ((sx >> 4) & 0x01010101u) + 5u * ((nx >> 4) & kLowNib) + ((ny >> 4) & kLowNib);
 
+    // adoption draws: both calls whenever the word has an active site (as in unit_flips)
     const uint32_t g0 = 2u * static_cast<uint32_t>(u.gw);
     const uint32_t kl = static_cast<uint32_t>(u.k), kh = static_cast<uint32_t>(u.k >> 32) | kTagU;
     uint4 u0 = make_uint4(g0, u.a, kl, kh), u1 = make_uint4(g0 + 1u, u.a, kl, kh);
-    const bool need0 = (active & 0x0000FFFFu) != 0, need1 = (active & 0xFFFF0000u) != 0;
-    if (need0 && need1) {
-        philox_rk2(u0, u1, rk);
-    } else {
-        const uint4 r = philox_rk(need0 ? u0 : u1, rk);
-        if (need0) u0 = r; else u1 = r;
-    }
+    philox_rk2(u0, u1, rk);
 
     uint32_t flips = 0;
 #define PGG_SITE(M, IREG, BYTE, UW)                                                 \
