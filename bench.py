@@ -39,15 +39,15 @@ FALLBACK_HBM_GBS = 6800.0
 # ALU pipe / of the FMA-heavy pipe (integer multiply-adds), dram_bytes = dram__bytes_read.sum +
 # dram__bytes_write.sum.
 NCU = {
-    "direct:7ddfd94ea47717a8:bitpack:8192:1:4:64":
-        {"alu_warp_inst": 4554560, "fma_warp_inst": 3904416, "dram_bytes": 8451584},
-    "resident:714b1d3e9c1ca6e4:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 69189494, "fma_warp_inst": 55686096, "dram_bytes": 8491520},
+    "direct:7a5d40e3f43095b2:bitpack:8192:1:4:64":
+        {"alu_warp_inst": 4130432, "fma_warp_inst": 3482656, "dram_bytes": 8448000},
+    "resident:11a1a0f693d3add9:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 60770262, "fma_warp_inst": 50489612, "dram_bytes": 8483584},
     # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
-    "resident:714b1d3e9c1ca6e4:u8:8192:16:152:0":
-        {"alu_warp_inst": 69189494, "fma_warp_inst": 55686096, "dram_bytes": 8491520},
-    "resident-pairwise:714b1d3e9c1ca6e4:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 61367898, "fma_warp_inst": None, "dram_bytes": 8479232},
+    "resident:11a1a0f693d3add9:u8:8192:16:152:0":
+        {"alu_warp_inst": 60770262, "fma_warp_inst": 50489612, "dram_bytes": 8483584},
+    "resident-pairwise:11a1a0f693d3add9:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 48876533, "fma_warp_inst": None, "dram_bytes": 8469248},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
