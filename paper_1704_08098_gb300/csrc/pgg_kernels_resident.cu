@@ -93,10 +93,22 @@ __device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
     return b;
 }
 
+// Words per task of the interior phase: 4 when that still gives every thread a task, else
+// fewer, so that small phases spread over all warps instead of a few long tasks.
+__device__ __forceinline__ int interior_task_words(int words) {
+    return words >= kResMaxUPT * kComputeThreads ? kResMaxUPT : (words >= 2 * kComputeThreads ? 2 : 1);
+}
+
 // Update the interior sublattice rows of the band (edge = false) or its edge rows (edge = true:
 // row 0 when in_lo = 1, row n_srows - 1 when in_hi < n_srows; never the same row twice, since
 // in_hi >= in_lo). Rows of one sublattice step are 4 apart and an update reads 3 rows either
 // side, so the two calls touch disjoint sites and need no barrier between them.
+//
+// The interior tasks go to threads 0, 1, ... in turn, so when their number n_int is not a
+// multiple of the thread count, threads f = n_int mod T and up have one task fewer. The edge
+// tasks are dealt to those threads first (task e to thread f + e, wrapping), with as few words
+// per task as still fit them: the edge rows then fill the gap of the last interior round instead
+// of forming a round of their own.
 template <int OJ, int GAME>
 __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *__restrict__ s_table,
                                               const PhiloxKeys &rk, int Lw, int r0, int nb, const BandRows &br,
@@ -105,14 +117,23 @@ __device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *
     // edge: selected row q is 0 or n_srows - 1 (edge_top: whether row 0 is one of them)
     const bool edge_top = br.in_lo != 0, edge_bot = br.in_hi < br.n_srows;
     const int n_rows_sel = edge ? static_cast<int>(edge_top) + static_cast<int>(edge_bot) : br.in_hi - br.in_lo;
-    // words per task: 4 when that still gives every thread a task, else fewer, so that the small
-    // phases (edge rows, small bands) spread over all warps instead of a few long tasks
     const int words = n_rows_sel * Lw;
-    const int upt = words >= kResMaxUPT * kComputeThreads ? kResMaxUPT : (words >= 2 * kComputeThreads ? 2 : 1);
+    int upt, shift = 0;
+    if (edge) {
+        const int int_words = (br.in_hi - br.in_lo) * Lw;
+        const int f = (int_words / interior_task_words(int_words)) % kComputeThreads;
+        const int free_threads = f ? kComputeThreads - f : kComputeThreads;
+        upt = words <= free_threads ? 1 : (words <= 2 * free_threads ? 2 : kResMaxUPT);
+        shift = f;
+    } else {
+        upt = interior_task_words(words);
+    }
     const int runs = Lw / upt;
     const int n_tasks = n_rows_sel * runs;
     const uint32_t kl = static_cast<uint32_t>(k), kh = static_cast<uint32_t>(k >> 32) | kTagDir;
-    for (int t = threadIdx.x; t < n_tasks; t += kComputeThreads) {
+    int t0 = static_cast<int>(threadIdx.x) - shift;
+    if (t0 < 0) t0 += kComputeThreads;
+    for (int t = t0; t < n_tasks; t += kComputeThreads) {
         const int q_sel = t / runs;
         const int sr = edge ? ((q_sel == 0 && edge_top) ? 0 : br.n_srows - 1) : br.in_lo + q_sel;
         const int c = t - q_sel * runs;
