@@ -267,12 +267,19 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         mbar_init(&s_mbar, 1);
     }
     // stage the table and band + halo (rows r0 - 3 .. r0 + nb + 2, periodic) with 4-byte
-    // asynchronous copies (cp.async: many loads in flight per thread, each word to its place)
-    for (int x = tid; x < (nb + 6) * Lw; x += kResThreads) {
-        const int lr = x / Lw, w = x - lr * Lw;
-        const int g = wrap_small(r0 - 3 + lr, L);
-        if (index_ok(static_cast<long long>(g) * Lw + w, static_cast<long long>(L) * Lw, p.status))
-            copy_async4(&s_rows[lr * Lw + swz(w)], &p.lat[static_cast<size_t>(g) * Lw + w]);
+    // asynchronous copies (cp.async: many loads in flight per thread, each word to its place);
+    // thread t copies column t mod Lw of every (T / Lw)-th row, so a copy costs a few adds
+    const int rows_per_pass = kResThreads / Lw;   // >= 1: a resident row has at most 448 words
+    const int col = tid % Lw, row_first = tid / Lw;
+    const int scol = swz(col);
+    if (row_first < rows_per_pass) {
+        int g = wrap_small(r0 - 3 + row_first, L);
+        for (int lr = row_first; lr < nb + 6; lr += rows_per_pass) {
+            if (index_ok(static_cast<long long>(g) * Lw + col, static_cast<long long>(L) * Lw, p.status))
+                copy_async4(&s_rows[lr * Lw + scol], &p.lat[static_cast<size_t>(g) * Lw + col]);
+            g += rows_per_pass;
+            if (g >= L) g -= L;
+        }
     }
     copy_async_wait_all();
     fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
@@ -387,11 +394,12 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         }
     }
     __syncthreads();  // the last bulk store has completed (its issuer waited) before the band is stored
-    // store the band
-    for (int x = tid; x < nb * Lw; x += kResThreads) {
-        const int lr = x / Lw, w = x - lr * Lw;
-        if (index_ok(static_cast<long long>(r0 + lr) * Lw + w, static_cast<long long>(L) * Lw, p.status))
-            p.lat[static_cast<size_t>(r0 + lr) * Lw + w] = s_rows[(lr + 3) * Lw + swz(w)];
+    // store the band (the same column-per-thread walk)
+    if (row_first < rows_per_pass) {
+        for (int lr = row_first; lr < nb; lr += rows_per_pass) {
+            if (index_ok(static_cast<long long>(r0 + lr) * Lw + col, static_cast<long long>(L) * Lw, p.status))
+                p.lat[static_cast<size_t>(r0 + lr) * Lw + col] = s_rows[(lr + 3) * Lw + scol];
+        }
     }
 }
 
