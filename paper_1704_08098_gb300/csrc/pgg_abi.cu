@@ -129,6 +129,7 @@ struct pgg_ctx {
     uint32_t *mailbox_d = nullptr;
     uint32_t *packed_d = nullptr;  // bit-packed copy of a uint8 lattice during a resident call
     unsigned int *ctr_d = nullptr;
+    unsigned int ctr_launches = 0;  // resident launches since ctr_d was last zeroed
     int *status_d = nullptr;
     unsigned int spin_limit = 1u << 22;
 };
@@ -420,6 +421,11 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             a.n_mcs = static_cast<int>(std::min<int64_t>(n_mcs - m0, 1 << 16));
             a.counts = c->counts_d + m0;
             a.k0 = c->step;
+            // a launch covers at most 2^20 steps: counters of launch n lie in [n 2^21, n 2^21 + 2^20]
+            if (c->ctr_launches == 0 || c->ctr_launches >= 2047) c->ctr_launches = 0;
+            a.reset_ctr = c->ctr_launches == 0;
+            a.ctr_base = c->ctr_launches << 21;
+            ++c->ctr_launches;
             PGG_CUDA(pgg::launch_resident(a, c->stream));
             c->step += 16ull * static_cast<uint64_t>(a.n_mcs);
         }

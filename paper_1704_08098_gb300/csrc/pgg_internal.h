@@ -83,6 +83,9 @@ struct ResidentArgs {
     const uint32_t *table;
     uint32_t *mailbox;            // resident_mailbox_words(L, n_bands) words
     unsigned int *ctr;            // n_bands counters
+    unsigned int ctr_base;        // a launch publishes ctr_base + completed steps: every value an
+                                  // earlier launch left is below it, so ctr needs no reset
+    bool reset_ctr;               // zero ctr before the launch (first use, or ctr_base wrapped)
     unsigned long long *counts;   // n_mcs counts, zeroed by the caller
     int *status;                  // | 1 a bounded wait ran out, | 2 the alignment check failed, | 4 an index
                                   // check failed (checked build)

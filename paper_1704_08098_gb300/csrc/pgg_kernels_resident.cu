@@ -45,7 +45,8 @@ struct ResidentParams {
     int n_mcs;
     const uint32_t *table;
     uint32_t *mailbox;        // [band][parity][top/bottom][3 rows][Lw]
-    unsigned int *ctr;        // [band] completed steps
+    unsigned int *ctr;        // [band] ctr_base + completed steps of this launch
+    unsigned int ctr_base;    // above every value an earlier launch left in ctr
     unsigned long long *counts;  // [n_mcs], zeroed before the launch
     int *status;              // 1: a wait timed out; | 4: an index check failed (checked build)
     unsigned int spin_limit;
@@ -294,8 +295,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
             // fetch the neighbours' rows after step j - 1 into the halo, asynchronously
             if (tid == kComputeThreads && j > 0) {
                 unsigned int it = 0;
-                while ((load_acquire(&p.ctr[up]) < static_cast<unsigned int>(j) ||
-                        load_acquire(&p.ctr[down]) < static_cast<unsigned int>(j)) && it < p.spin_limit) {
+                const unsigned int want = p.ctr_base + static_cast<unsigned int>(j);
+                while ((load_acquire(&p.ctr[up]) < want || load_acquire(&p.ctr[down]) < want) && it < p.spin_limit) {
                     __nanosleep(32);
                     ++it;
                 }
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 bulk_commit_and_wait();
                 fence_async_global();
                 __threadfence();
-                store_release(&p.ctr[b], static_cast<unsigned int>(j + 1));
+                store_release(&p.ctr[b], p.ctr_base + static_cast<unsigned int>(j + 1));
             }
             __syncwarp();
         } else if ((j & 15) == 15 && p.counts) {
@@ -433,6 +434,7 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.table = a.table;
     p.mailbox = a.mailbox;
     p.ctr = a.ctr;
+    p.ctr_base = a.ctr_base;
     p.counts = a.counts;
     p.status = a.status;
     p.spin_limit = a.spin_limit;
@@ -443,8 +445,10 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
                                              : reinterpret_cast<const void *>(k_resident<kGroupGame>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.ctr, 0, sizeof(unsigned int) * a.n_bands, s);
-    if (e != cudaSuccess) return e;
+    if (a.reset_ctr) {
+        e = cudaMemsetAsync(a.ctr, 0, sizeof(unsigned int) * a.n_bands, s);
+        if (e != cudaSuccess) return e;
+    }
     void *args[] = {&p};
     return cudaLaunchCooperativeKernel(kernel, dim3(a.n_bands), dim3(kResThreads), args, smem, s);
 }
