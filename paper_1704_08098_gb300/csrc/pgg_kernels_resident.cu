@@ -22,9 +22,10 @@
 // Per step the work is the direct kernel's: tasks of one sublattice row and 1-4 words, the shared
 // update core of pgg_unit.cuh, in place in shared memory. A step first updates the band's
 // interior sublattice rows, whose reads stay inside the band, and only then waits for the
-// neighbours and refreshes the halo for the at most two edge rows: the wait overlaps work. The
-// count after each MCS is the sum of the bands' population counts.
-#include <cooperative_groups.h>
+// neighbours and refreshes the halo for the at most two edge rows: the wait overlaps work (the
+// edge rows go to the threads the interior leaves one task short). The count after each MCS is
+// the sum of the bands' population counts. The band is staged with 4-byte cp.async copies and
+// written back once per launch.
 #include <cuda_runtime.h>
 
 #include "pgg_device.cuh"
@@ -48,7 +49,7 @@ struct ResidentParams {
     unsigned int *ctr;        // [band] ctr_base + completed steps of this launch
     unsigned int ctr_base;    // above every value an earlier launch left in ctr
     unsigned long long *counts;  // [n_mcs], zeroed before the launch
-    int *status;              // 1: a wait timed out; | 4: an index check failed (checked build)
+    int *status;              // | 1 a wait timed out, | 2 misaligned buffers, | 4 an index check failed (checked build)
     unsigned int spin_limit;
     PhiloxKeys rk;
 };
