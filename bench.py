@@ -41,13 +41,13 @@ FALLBACK_HBM_GBS = 6800.0
 NCU = {
     "direct:7a5d40e3f43095b2:bitpack:8192:1:4:64":
         {"alu_warp_inst": 4130432, "fma_warp_inst": 3482656, "dram_bytes": 8448000},
-    "resident:e2f978519621a96e:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 59757355, "fma_warp_inst": 47346078, "dram_bytes": 8484864},
+    "resident:64574bf3dd02e9bf:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 59757347, "fma_warp_inst": 47346056, "dram_bytes": 8484864},
     # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
-    "resident:e2f978519621a96e:u8:8192:16:152:0":
-        {"alu_warp_inst": 59757355, "fma_warp_inst": 47346078, "dram_bytes": 8484864},
-    "resident-pairwise:e2f978519621a96e:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 47541669, "fma_warp_inst": None, "dram_bytes": 8469760},
+    "resident:64574bf3dd02e9bf:u8:8192:16:152:0":
+        {"alu_warp_inst": 59757347, "fma_warp_inst": 47346056, "dram_bytes": 8484864},
+    "resident-pairwise:64574bf3dd02e9bf:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 47541529, "fma_warp_inst": None, "dram_bytes": 8469760},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
