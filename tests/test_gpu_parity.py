@@ -364,6 +364,21 @@ def test_beyond_resident_sizes_default_schedule(o, pgg, L):
     assert np.array_equal(got_lat, want_lat)
 
 
+def test_resident_many_launches(o, pgg):
+    """2100 one-MCS calls on one context: the neighbour counters carry a per-launch base that
+    wraps (and is reset) after 2047 launches; the trajectory must not notice."""
+    L, n = 256, 2100
+    want_lat, want_counts = run_oracle(o, L, 3.9, 0.5, 17, n)
+    with pgg.Lattice(L, 3.9, 0.5, layout="bitpack") as lat:
+        lat.set_schedule("resident")
+        lat.seed(17, 0.5)
+        counts = np.concatenate([lat.step_mcs(1) for _ in range(n)])
+        got, step = lat.get()
+    assert step == 16 * n
+    assert np.array_equal(counts, want_counts)
+    assert np.array_equal(got, want_lat)
+
+
 def test_resident_wait_timeout_is_reported(o, pgg):
     """A bounded wait that runs out (spin limit 0: every wait gives up at once) returns
     PGG_ERR_TIMEOUT at the next synchronising call; the context stays usable."""
