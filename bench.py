@@ -438,24 +438,55 @@ def main():
                                f"{sched['tile_y']})", "launch_ms": launch_s * 1e3,
                      "ncu_key": key, "hbm_model": hbm_model})
 
-    # end to end through the public API with host buffers: upload the lattice from pinned
-    # memory, run one MCS, read the count back
-    # (the lattice travels in its bit-packed host form, L*L/8 bytes, for either device layout)
+    # end to end through the public API with host buffers: every step uploads its input lattice
+    # from pinned memory (in its bit-packed host form, L*L/8 bytes, for either device layout),
+    # runs one MCS and reads its cooperator count back to the host
     e2e = None
     if not args.no_e2e:
         host_words, _ = lat.get_packed()
         pinned = torch.from_numpy(host_words.reshape(-1).view(np.int32)).pin_memory()
-        upload, h2d, how = lat.set_packed_from_pointer, L * L // 8, "pgg_set_lattice_packed(pinned host, L*L/8 bytes)"
+        h2d = L * L // 8
+        reps = 50
+        # serial: synchronous upload, one MCS, the count read back by the same call
         counts = np.zeros(1, dtype=np.uint64)
-        reps = max(3, min(args.steps, 10))
+        lat.set_packed_from_pointer(pinned.data_ptr(), 0)   # untimed: first-use buffers
+        lat.step_mcs(1, counts)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
-            upload(pinned.data_ptr(), 0)
+            lat.set_packed_from_pointer(pinned.data_ptr(), 0)
             lat.step_mcs(1, counts)
+        serial = L * L * reps / (time.perf_counter() - t0)
+        # overlapped: step i+1's input is staged on the context's copy stream while step i runs;
+        # each count goes to pinned host memory and the host reads count i-1 once step i is queued
+        dev_counts = torch.zeros(reps, dtype=torch.int64, device="cuda")
+        host_counts = torch.zeros(reps, dtype=torch.int64).pin_memory()
+        done = [torch.cuda.Event() for _ in range(reps)]
+        read = []
+        lat.stage_packed_from_pointer(pinned.data_ptr(), 0)   # untimed: copy stream and buffers
+        lat.step_mcs(1, dev_counts[0].data_ptr())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(reps):
+            lat.stage_packed_from_pointer(pinned.data_ptr(), 0)
+            lat.step_mcs(1, dev_counts[i].data_ptr())
+            host_counts[i].copy_(dev_counts[i], non_blocking=True)
+            done[i].record(stream)
+            if i > 0:
+                done[i - 1].synchronize()
+                read.append(int(host_counts[i - 1]))
+        done[-1].synchronize()
+        read.append(int(host_counts[-1]))
         el = time.perf_counter() - t0
+        # every step advanced the same input from the same step counter: one count
+        assert len(set(read)) == 1 and read[0] == int(counts[0]), "end-to-end steps disagree"
         e2e = {"value": L * L * reps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 8, "path": how + " + pgg_step_mcs(1, host counts)"}
+               "d2h_bytes_per_step": 8, "steps": reps,
+               "path": "pgg_stage_lattice_packed(pinned host, L*L/8 bytes) + pgg_step_mcs(1, device "
+                       "count) + count copied to pinned host memory and read each step; the upload "
+                       "of step i+1 overlaps step i",
+               "serial": {"value": serial, "path": "pgg_set_lattice_packed (synchronous) + "
+                                                   "pgg_step_mcs(1, host count)"}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

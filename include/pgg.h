@@ -141,7 +141,8 @@ int pgg_seed(pgg_ctx *ctx, uint64_t seed, double p);
  * coop_per_mcs (nullable) receives n_mcs uint64 cooperator counts (numerator of
  * Eq. (4)), the count after each MCS; it may be device memory (written
  * asynchronously) or host memory (the call then synchronises the stream before
- * returning). n_mcs >= 0; n_mcs == 0 is a no-op. */
+ * returning, and also reports a failed bounded wait or index check of this call's
+ * kernels). n_mcs >= 0; n_mcs == 0 is a no-op. */
 int pgg_step_mcs(pgg_ctx *ctx, int64_t n_mcs, uint64_t *coop_per_mcs);
 
 /* Number of cooperators now (numerator of Eq. (4)) into *out (host). Synchronises the
@@ -164,6 +165,20 @@ int pgg_set_lattice(pgg_ctx *ctx, const uint8_t *host_in, uint64_t step);
  * stream. */
 int pgg_get_lattice_packed(pgg_ctx *ctx, uint32_t *host_words_out, uint64_t *step_out);
 int pgg_set_lattice_packed(pgg_ctx *ctx, const uint32_t *host_words_in, uint64_t step);
+
+/* Overlapped upload: queue the copy of host_words_in (bit-packed as above, L*L/8 bytes) on a
+ * copy stream of the context's own and return without waiting, so that the copy runs while
+ * work already queued on the context stream computes. The staged lattice and `step` replace the
+ * context's lattice and step counter at the next call that reads or writes them (pgg_step_mcs,
+ * pgg_count_coop, the get/set calls, pgg_seed, pgg_autotune, pgg_lattice_device_ptr), in stream
+ * order: that call's work waits for the copy. pgg_get_state reports the staged step at once.
+ * Two device buffers alternate, so a loop of stage / step calls overlaps the upload of the next
+ * input with the current step. host_words_in should be pinned memory (from pageable memory the
+ * copy cannot overlap) and must stay valid and unchanged until the copy has completed: at the
+ * latest when a synchronising call after the applying call has returned, or when an event recorded
+ * on the context stream after the applying call has completed. Need L % 32 == 0 and step < 2^56;
+ * PGG_ERR_STATE if a staged lattice has not been applied yet. */
+int pgg_stage_lattice_packed(pgg_ctx *ctx, const uint32_t *host_words_in, uint64_t step);
 
 /* Current seed and step counter. */
 int pgg_get_state(const pgg_ctx *ctx, uint64_t *seed_out, uint64_t *step_out);

@@ -131,7 +131,19 @@ struct pgg_ctx {
     unsigned int *ctr_d = nullptr;
     unsigned int ctr_launches = 0;  // resident launches since ctr_d was last zeroed
     int *status_d = nullptr;
+    int *status_h = nullptr;                  // pinned: the status word read back with the counts
+    unsigned long long *counts_h = nullptr;   // pinned: counts on their way to a host buffer
+    int64_t counts_h_cap = 0;
     unsigned int spin_limit = 1u << 22;
+    // overlapped upload (pgg_stage_lattice_packed): two bit-packed buffers filled by a copy
+    // stream of the context's own while the context stream computes
+    cudaStream_t copy_stream = nullptr;
+    uint32_t *stage_d[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ready[2] = {nullptr, nullptr};  // the copy into stage_d[b] has completed
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};   // the context stream has read stage_d[b]
+    int stage_next = 0;        // buffer the next pgg_stage_lattice_packed fills
+    int stage_pending = -1;    // buffer holding a staged lattice not yet applied, or -1
+    uint64_t stage_step = 0;   // step counter that comes with the staged lattice
 };
 
 namespace {
@@ -224,11 +236,42 @@ int ensure_staging(pgg_ctx *c) {
     return PGG_OK;
 }
 
+int ensure_stage(pgg_ctx *c) {
+    if (c->copy_stream) return PGG_OK;
+    const size_t bytes = static_cast<size_t>(c->L) * c->L / 8;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        if ((e = cudaMalloc(&c->stage_d[b], bytes)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&c->stage_ready[b], cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaEventCreateWithFlags(&c->stage_free[b], cudaEventDisableTiming)) != cudaSuccess) break;
+        e = cudaEventRecord(c->stage_free[b], c->stream);  // both buffers start free
+    }
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PGG_ERR_OOM : PGG_ERR_CUDA,
+                                      "pgg_stage_lattice_packed: copy stream, buffers or events: %s", cudaGetErrorString(e));
+    return PGG_OK;
+}
+
+// Make a staged lattice the context's lattice, in stream order: the context stream waits for
+// its copy, moves it into the lattice (unpacking it for a uint8 lattice) and releases the
+// buffer for a later stage call. Every entry point that reads or writes the lattice or the
+// step counter calls this first.
+int apply_stage(pgg_ctx *c) {
+    const int b = c->stage_pending;
+    if (b < 0) return PGG_OK;
+    c->stage_pending = -1;
+    PGG_CUDA(cudaStreamWaitEvent(c->stream, c->stage_ready[b], 0));
+    if (c->layout == PGG_BITPACK)
+        PGG_CUDA(cudaMemcpyAsync(c->lat, c->stage_d[b], c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    else
+        PGG_CUDA(pgg::launch_unpack(c->stage_d[b], static_cast<uint8_t *>(c->lat), c->L, c->stream));
+    PGG_CUDA(cudaEventRecord(c->stage_free[b], c->stream));
+    c->step = c->stage_step;
+    c->running_valid = false;
+    return PGG_OK;
+}
+
 // Report (and clear) a bounded wait that ran out in an earlier resident launch.
-int check_status(pgg_ctx *c) {
-    int st = 0;
-    PGG_CUDA(cudaMemcpyAsync(&st, c->status_d, sizeof st, cudaMemcpyDeviceToHost, c->stream));
-    PGG_CUDA(cudaStreamSynchronize(c->stream));
+int status_result(pgg_ctx *c, int st) {
     if (st) {
         PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
         PGG_CUDA(cudaStreamSynchronize(c->stream));
@@ -245,6 +288,41 @@ int check_status(pgg_ctx *c) {
                     c->spin_limit);
     }
     return PGG_OK;
+}
+
+int check_status(pgg_ctx *c) {
+    PGG_CUDA(cudaMemcpyAsync(c->status_h, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    return status_result(c, *c->status_h);
+}
+
+bool is_device_pointer(const void *p);
+
+// Hand the n counts of a pgg_step_mcs call to the caller. Device memory is filled
+// asynchronously. Host memory is filled through a pinned buffer, with the status word read
+// back by the same synchronisation, so that a failed bounded wait or index check is reported by
+// this call.
+int deliver_counts(pgg_ctx *c, uint64_t *out, int64_t n) {
+    const size_t bytes = static_cast<size_t>(n) * sizeof(uint64_t);
+    if (is_device_pointer(out)) {
+        PGG_CUDA(cudaMemcpyAsync(out, c->counts_d, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        return PGG_OK;
+    }
+    if (n > c->counts_h_cap) {
+        int64_t cap = c->counts_h_cap > 0 ? c->counts_h_cap : 1024;
+        while (cap < n) cap *= 2;
+        if (c->counts_h) cudaFreeHost(c->counts_h);
+        c->counts_h = nullptr;
+        c->counts_h_cap = 0;
+        cudaError_t e = cudaMallocHost(&c->counts_h, static_cast<size_t>(cap) * sizeof(unsigned long long));
+        if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMallocHost(counts, %lld): %s", (long long)cap, cudaGetErrorString(e));
+        c->counts_h_cap = cap;
+    }
+    PGG_CUDA(cudaMemcpyAsync(c->counts_h, c->counts_d, bytes, cudaMemcpyDeviceToHost, c->stream));
+    PGG_CUDA(cudaMemcpyAsync(c->status_h, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, c->counts_h, bytes);
+    return status_result(c, *c->status_h);
 }
 
 // Rebuild the host table for the context's game and parameters and copy it to the device.
@@ -310,7 +388,8 @@ int pgg_create(pgg_ctx **out, int L, double r, double K, int layout, void *cuda_
     pgg::build_threshold_table(r, K, c->table_h);
     if ((e = cudaMalloc(&c->lat, c->lat_bytes)) != cudaSuccess ||
         (e = cudaMalloc(&c->table_d, sizeof c->table_h)) != cudaSuccess ||
-        (e = cudaMalloc(&c->status_d, sizeof(int))) != cudaSuccess) {
+        (e = cudaMalloc(&c->status_d, sizeof(int))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->status_h, sizeof(int))) != cudaSuccess) {
         pgg_destroy(c);
         return fail(PGG_ERR_OOM, "pgg_create: cudaMalloc: %s", cudaGetErrorString(e));
     }
@@ -365,6 +444,7 @@ int pgg_seed(pgg_ctx *c, uint64_t seed, double p) {
     if (!c) return fail(PGG_ERR_ARG, "pgg_seed: NULL context");
     if (!(p >= 0.0 && p <= 1.0)) return fail(PGG_ERR_ARG, "pgg_seed: p must be in [0, 1]");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     uint64_t thr = p >= 1.0 ? (1ull << 32) : static_cast<uint64_t>(p * 4294967296.0);
     PGG_CUDA(pgg::launch_init(c->layout, c->lat, c->L, seed, thr, c->stream));
     c->seed = seed;
@@ -378,9 +458,11 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     if (!c) return fail(PGG_ERR_ARG, "pgg_step_mcs: NULL context");
     if (n_mcs < 0) return fail(PGG_ERR_ARG, "pgg_step_mcs: n_mcs < 0");
     if (n_mcs == 0) return PGG_OK;
-    if (c->step + 16ull * static_cast<uint64_t>(n_mcs) >= kMaxStep)
+    const uint64_t step_in = c->stage_pending >= 0 ? c->stage_step : c->step;
+    if (step_in + 16ull * static_cast<uint64_t>(n_mcs) >= kMaxStep)
         return fail(PGG_ERR_ARG, "pgg_step_mcs: step counter would pass 2^56");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     int rc = ensure_counts(c, n_mcs);
     if (rc) return rc;
     const Schedule s = resolve_schedule(c);
@@ -432,18 +514,8 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         if (c->layout == PGG_U8)
             PGG_CUDA(pgg::launch_unpack(packed, static_cast<uint8_t *>(c->lat), c->L, c->stream));
         c->running_valid = false;
-        if (coop_per_mcs) {
-            const size_t bytes = static_cast<size_t>(n_mcs) * sizeof(uint64_t);
-            if (is_device_pointer(coop_per_mcs)) {
-                PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            } else {
-                PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToHost, c->stream));
-                PGG_CUDA(cudaStreamSynchronize(c->stream));
-                return check_status(c);
-            }
-        }
         PGG_CUDA(cudaGetLastError());
-        return PGG_OK;
+        return coop_per_mcs ? deliver_counts(c, coop_per_mcs, n_mcs) : PGG_OK;
     }
     if (s.kernel == PGG_KERNEL_DIRECT) {
         if (!c->running_d) {
@@ -500,23 +572,15 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             }
         }
     }
-    if (coop_per_mcs) {
-        const size_t bytes = static_cast<size_t>(n_mcs) * sizeof(uint64_t);
-        if (is_device_pointer(coop_per_mcs)) {
-            PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        } else {
-            PGG_CUDA(cudaMemcpyAsync(coop_per_mcs, c->counts_d, bytes, cudaMemcpyDeviceToHost, c->stream));
-            PGG_CUDA(cudaStreamSynchronize(c->stream));
-        }
-    }
     PGG_CUDA(cudaGetLastError());
-    return PGG_OK;
+    return coop_per_mcs ? deliver_counts(c, coop_per_mcs, n_mcs) : PGG_OK;
 }
 
 int pgg_count_coop(pgg_ctx *c, uint64_t *out) {
     g_last_error.clear();
     if (!c || !out) return fail(PGG_ERR_ARG, "pgg_count_coop: NULL argument");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     int rc = ensure_counts(c, 1);
     if (rc) return rc;
     PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, sizeof(unsigned long long), c->stream));
@@ -532,6 +596,7 @@ int pgg_get_lattice(pgg_ctx *c, uint8_t *host_out, uint64_t *step_out) {
     g_last_error.clear();
     if (!c || !host_out) return fail(PGG_ERR_ARG, "pgg_get_lattice: NULL argument");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     const size_t n = static_cast<size_t>(c->L) * c->L;
     if (c->layout == PGG_U8) {
         PGG_CUDA(cudaMemcpyAsync(host_out, c->lat, n, cudaMemcpyDeviceToHost, c->stream));
@@ -551,6 +616,7 @@ int pgg_set_lattice(pgg_ctx *c, const uint8_t *host_in, uint64_t step) {
     if (!c || !host_in) return fail(PGG_ERR_ARG, "pgg_set_lattice: NULL argument");
     if (step >= kMaxStep) return fail(PGG_ERR_ARG, "pgg_set_lattice: step >= 2^56");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     const size_t n = static_cast<size_t>(c->L) * c->L;
     if (c->layout == PGG_U8) {
         PGG_CUDA(cudaMemcpyAsync(c->lat, host_in, n, cudaMemcpyHostToDevice, c->stream));
@@ -572,6 +638,7 @@ int pgg_get_lattice_packed(pgg_ctx *c, uint32_t *host_words_out, uint64_t *step_
     if (!c || !host_words_out) return fail(PGG_ERR_ARG, "pgg_get_lattice_packed: NULL argument");
     if (c->L % 32 != 0) return fail(PGG_ERR_ARG, "pgg_get_lattice_packed: needs L %% 32 == 0 (L = %d)", c->L);
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     const size_t bytes = static_cast<size_t>(c->L) * c->L / 8;
     if (c->layout == PGG_BITPACK) {
         PGG_CUDA(cudaMemcpyAsync(host_words_out, c->lat, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -593,6 +660,7 @@ int pgg_set_lattice_packed(pgg_ctx *c, const uint32_t *host_words_in, uint64_t s
     if (c->L % 32 != 0) return fail(PGG_ERR_ARG, "pgg_set_lattice_packed: needs L %% 32 == 0 (L = %d)", c->L);
     if (step >= kMaxStep) return fail(PGG_ERR_ARG, "pgg_set_lattice_packed: step >= 2^56");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     const size_t bytes = static_cast<size_t>(c->L) * c->L / 8;
     if (c->layout == PGG_BITPACK) {
         PGG_CUDA(cudaMemcpyAsync(c->lat, host_words_in, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -609,11 +677,33 @@ int pgg_set_lattice_packed(pgg_ctx *c, const uint32_t *host_words_in, uint64_t s
     return PGG_OK;
 }
 
+
+int pgg_stage_lattice_packed(pgg_ctx *c, const uint32_t *host_words_in, uint64_t step) {
+    g_last_error.clear();
+    if (!c || !host_words_in) return fail(PGG_ERR_ARG, "pgg_stage_lattice_packed: NULL argument");
+    if (c->L % 32 != 0) return fail(PGG_ERR_ARG, "pgg_stage_lattice_packed: needs L %% 32 == 0 (L = %d)", c->L);
+    if (step >= kMaxStep) return fail(PGG_ERR_ARG, "pgg_stage_lattice_packed: step >= 2^56");
+    if (c->stage_pending >= 0)
+        return fail(PGG_ERR_STATE, "pgg_stage_lattice_packed: a staged lattice is still waiting for the call that applies it");
+    PGG_CUDA(cudaSetDevice(c->device));
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    const int b = c->stage_next;
+    PGG_CUDA(cudaStreamWaitEvent(c->copy_stream, c->stage_free[b], 0));
+    PGG_CUDA(cudaMemcpyAsync(c->stage_d[b], host_words_in, static_cast<size_t>(c->L) * c->L / 8,
+                             cudaMemcpyHostToDevice, c->copy_stream));
+    PGG_CUDA(cudaEventRecord(c->stage_ready[b], c->copy_stream));
+    c->stage_next = b ^ 1;
+    c->stage_pending = b;
+    c->stage_step = step;
+    return PGG_OK;
+}
+
 int pgg_get_state(const pgg_ctx *c, uint64_t *seed_out, uint64_t *step_out) {
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_get_state: NULL context");
     if (seed_out) *seed_out = c->seed;
-    if (step_out) *step_out = c->step;
+    if (step_out) *step_out = c->stage_pending >= 0 ? c->stage_step : c->step;
     return PGG_OK;
 }
 
@@ -691,6 +781,8 @@ int pgg_get_threshold_table(const pgg_ctx *c, uint32_t *host_out) {
 int pgg_lattice_device_ptr(pgg_ctx *c, void **dev_ptr, uint64_t *bytes) {
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_lattice_device_ptr: NULL context");
+    PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     if (dev_ptr) *dev_ptr = c->lat;
     if (bytes) *bytes = c->lat_bytes;
     return PGG_OK;
@@ -702,6 +794,7 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
     if (!c) return fail(PGG_ERR_ARG, "pgg_autotune: NULL context");
     if (n_mcs < 1 || n_mcs > 1000) return fail(PGG_ERR_ARG, "pgg_autotune: n_mcs must be in [1, 1000]");
     PGG_CUDA(cudaSetDevice(c->device));
+    if (int rc_stage = apply_stage(c)) return rc_stage;
     // candidates
     std::vector<Schedule> cand;
     if (pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) > 0) cand.push_back({PGG_KERNEL_RESIDENT, 16, 0, 0});
@@ -790,6 +883,15 @@ void pgg_destroy(pgg_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->stage_d[b]) cudaFree(c->stage_d[b]);
+        if (c->stage_ready[b]) cudaEventDestroy(c->stage_ready[b]);
+        if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
+    }
     if (c->lat) cudaFree(c->lat);
     if (c->lat_alt) cudaFree(c->lat_alt);
     if (c->table_d) cudaFree(c->table_d);
@@ -800,6 +902,8 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->packed_d) cudaFree(c->packed_d);
     if (c->ctr_d) cudaFree(c->ctr_d);
     if (c->status_d) cudaFree(c->status_d);
+    if (c->status_h) cudaFreeHost(c->status_h);
+    if (c->counts_h) cudaFreeHost(c->counts_h);
     delete c;
 }
 

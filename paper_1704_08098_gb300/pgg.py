@@ -57,6 +57,7 @@ def _declare(lib):
         "pgg_get_state": (ctypes.c_int, [_vp, _u64p, _u64p]),
         "pgg_get_lattice_packed": (ctypes.c_int, [_vp, _u32p, _u64p]),
         "pgg_set_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
+        "pgg_stage_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
         "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]),
         "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
@@ -269,6 +270,13 @@ class Lattice:
         """pgg_set_lattice_packed from a raw host pointer (e.g. pinned memory)."""
         self._check(self.lib.pgg_set_lattice_packed(self._h, ctypes.cast(host_ptr, _u32p), int(step)),
               "pgg_set_lattice_packed")
+
+    def stage_packed_from_pointer(self, host_ptr: int, step: int = 0) -> None:
+        """pgg_stage_lattice_packed from a raw host pointer (pinned memory, for the copy to
+        overlap the work already queued): the next step_mcs (or any call that reads the lattice)
+        starts from it. The buffer must stay unchanged until that call's work has run."""
+        self._check(self.lib.pgg_stage_lattice_packed(self._h, ctypes.cast(host_ptr, _u32p), int(step)),
+                    "pgg_stage_lattice_packed")
 
     def state(self) -> tuple[int, int]:
         seed, step = ctypes.c_uint64(), ctypes.c_uint64()

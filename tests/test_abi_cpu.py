@@ -55,6 +55,7 @@ def test_argument_validation_without_gpu(lib):
     assert lib.pgg_get_game(None, None, None) == pgg.PGG_ERR_ARG
     assert lib.pgg_set_lattice_packed(None, None, 0) == pgg.PGG_ERR_ARG
     assert lib.pgg_get_lattice_packed(None, None, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_stage_lattice_packed(None, None, 0) == pgg.PGG_ERR_ARG
     lib.pgg_destroy(None)
     assert lib.pgg_version().decode().startswith("pgg-gb300")
 

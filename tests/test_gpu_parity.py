@@ -222,6 +222,80 @@ def test_packed_host_transfers(o, pgg, layout):
     assert np.array_equal(bits.astype(np.uint8), ref)
 
 
+def pack_rows(lat):
+    L = lat.shape[0]
+    words = (lat.reshape(L, L // 32, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(-1)
+    return words.astype(np.uint32)
+
+
+@pytest.mark.parametrize("kernel", ["resident", "tiled", "direct"])
+@pytest.mark.parametrize("layout", ["bitpack", "u8"])
+def test_staged_uploads_overlap_steps(o, pgg, layout, kernel):
+    """pgg_stage_lattice_packed in a loop (stage input i, step it with counts into device memory,
+    read the counts back through pinned memory while the next input is staged): every input's
+    trajectory matches the oracle run from that input and step."""
+    import torch
+    if kernel == "direct" and layout == "u8":
+        pytest.skip("the direct kernel runs bit-packed lattices only")
+    L, n_mcs = 512, 3
+    lats = [inputs.random_lattice(L, p, seed=40 + i) for i, p in enumerate((0.5, 0.3, 0.7, 0.5, 0.45))]
+    steps = [0, 16 * 5, 16 * 11 + 0, 7 * 16, 16 * 1000]
+    host = [torch.from_numpy(pack_rows(x).reshape(-1).view(np.int32)).pin_memory() for x in lats]
+    dev = torch.zeros((len(lats), n_mcs), dtype=torch.int64, device="cuda")
+    back = torch.zeros((len(lats), n_mcs), dtype=torch.int64).pin_memory()
+    stream = torch.cuda.current_stream()
+    with pgg.Lattice(L, 3.9, 0.5, layout=layout, stream=stream.cuda_stream) as lat:
+        lat.set_schedule(kernel, 4 if kernel == "tiled" else 1)
+        lat.seed(9)
+        done = []
+        for i in range(len(lats)):
+            lat.stage_packed_from_pointer(host[i].data_ptr(), steps[i])
+            assert lat.state()[1] == steps[i]
+            lat.step_mcs(n_mcs, dev[i].data_ptr())
+            back[i].copy_(dev[i], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            done.append(ev)
+        done[-1].synchronize()
+        final, step = lat.get()
+    assert step == steps[-1] + 16 * n_mcs
+    for i, x in enumerate(lats):
+        ref = x.copy()
+        want = o.run(ref, 3.9, 0.5, 9, steps[i], n_mcs, threads=THREADS)
+        assert np.array_equal(back[i].numpy().astype(np.uint64), want), i
+    assert np.array_equal(final, ref)
+
+
+def test_staged_lattice_is_applied_by_every_reader(o, pgg):
+    """A staged lattice replaces the state at the next call that reads or writes it: get, count,
+    a second stage before it is applied is refused, pgg_seed overwrites it, and a context
+    destroyed with a staged lattice pending releases cleanly."""
+    import torch
+    L = 256
+    a = inputs.random_lattice(L, 0.35, seed=3)
+    b = inputs.random_lattice(L, 0.6, seed=4)
+    ha = torch.from_numpy(pack_rows(a).reshape(-1).view(np.int32)).pin_memory()
+    hb = torch.from_numpy(pack_rows(b).reshape(-1).view(np.int32)).pin_memory()
+    for layout in ("bitpack", "u8"):
+        with pgg.Lattice(L, 3.9, 0.5, layout=layout) as lat:
+            lat.seed(2)
+            lat.stage_packed_from_pointer(ha.data_ptr(), 48)
+            assert lat.state() == (2, 48)
+            with pytest.raises(pgg.PGGError) as e:
+                lat.stage_packed_from_pointer(hb.data_ptr(), 0)
+            assert e.value.status == pgg.PGG_ERR_STATE
+            got, step = lat.get()
+            assert step == 48 and np.array_equal(got, a)
+            lat.stage_packed_from_pointer(hb.data_ptr(), 16)
+            assert lat.count() == int(b.sum())
+            assert np.array_equal(lat.get()[0], b)
+            lat.stage_packed_from_pointer(ha.data_ptr(), 32)
+            lat.seed(2, 0.5)   # overwrites the staged lattice
+            seeded, step = lat.get()
+            assert step == 0 and np.array_equal(seeded, o.init(L, 2, 0.5))
+            lat.stage_packed_from_pointer(hb.data_ptr(), 64)   # left pending at destroy
+
+
 def test_layouts_and_schedules_agree_L1024(pgg):
     ref = None
     for layout in ("u8", "bitpack"):
@@ -364,6 +438,25 @@ def test_beyond_resident_sizes_default_schedule(o, pgg, L):
     assert np.array_equal(got_lat, want_lat)
 
 
+@pytest.mark.parametrize("kernel", ["resident", "direct", "tiled"])
+def test_set_params_mid_run(o, pgg, kernel):
+    """Changing r and K between calls (the annealing scan does) rebuilds the table for the next
+    call only; the trajectory matches the oracle run in two legs."""
+    L = 512
+    ref = o.init(L, 23, 0.5)
+    want = np.concatenate([o.run(ref, 4.2, 0.5, 23, 0, 4, threads=THREADS),
+                           o.run(ref, 3.8, 0.3, 23, 16 * 4, 5, threads=THREADS)])
+    with pgg.Lattice(L, 4.2, 0.5, layout="bitpack") as lat:
+        lat.set_schedule(kernel, 4 if kernel == "tiled" else 1)
+        lat.seed(23, 0.5)
+        c1 = lat.step_mcs(4)
+        lat.set_params(3.8, 0.3)
+        c2 = lat.step_mcs(5)
+        got, _ = lat.get()
+    assert np.array_equal(np.concatenate([c1, c2]), want)
+    assert np.array_equal(got, ref)
+
+
 def test_resident_many_launches(o, pgg):
     """2100 one-MCS calls on one context: the neighbour counters carry a per-launch base that
     wraps (and is reset) after 2047 launches; the trajectory must not notice."""
@@ -381,7 +474,8 @@ def test_resident_many_launches(o, pgg):
 
 def test_resident_wait_timeout_is_reported(o, pgg):
     """A bounded wait that runs out (spin limit 0: every wait gives up at once) returns
-    PGG_ERR_TIMEOUT at the next synchronising call; the context stays usable."""
+    PGG_ERR_TIMEOUT at the next synchronising call (the step call itself when it reads the counts
+    back to the host); the context stays usable."""
     with pgg.Lattice(1024, 3.9, 0.5, layout="bitpack") as lat:
         lat.set_schedule("resident")
         lat.seed(3, 0.5)
@@ -389,6 +483,10 @@ def test_resident_wait_timeout_is_reported(o, pgg):
         lat.advance(1)
         with pytest.raises(pgg.PGGError) as exc:
             lat.count()
+        assert exc.value.status == pgg.PGG_ERR_TIMEOUT
+        lat.seed(3, 0.5)
+        with pytest.raises(pgg.PGGError) as exc:   # with host counts, the step call reports it
+            lat.step_mcs(1)
         assert exc.value.status == pgg.PGG_ERR_TIMEOUT
         lat.set_spin_limit(1 << 22)
         lat.seed(3, 0.5)
