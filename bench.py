@@ -39,15 +39,15 @@ FALLBACK_HBM_GBS = 6800.0
 # ALU pipe / of the FMA-heavy pipe (integer multiply-adds), dram_bytes = dram__bytes_read.sum +
 # dram__bytes_write.sum.
 NCU = {
-    "direct:7a5d40e3f43095b2:bitpack:8192:1:4:64":
-        {"alu_warp_inst": 4130432, "fma_warp_inst": 3482656, "dram_bytes": 8448000},
-    "resident:64574bf3dd02e9bf:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 59757347, "fma_warp_inst": 47346056, "dram_bytes": 8484864},
+    "direct:1385c7b1fc7d18a3:bitpack:8192:1:4:64":
+        {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
+    "resident:6e3adf86db1b26bb:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 56014758, "fma_warp_inst": 44574310, "dram_bytes": 8481792},
     # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
-    "resident:64574bf3dd02e9bf:u8:8192:16:152:0":
-        {"alu_warp_inst": 59757347, "fma_warp_inst": 47346056, "dram_bytes": 8484864},
-    "resident-pairwise:64574bf3dd02e9bf:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 47541529, "fma_warp_inst": None, "dram_bytes": 8469760},
+    "resident:6e3adf86db1b26bb:u8:8192:16:152:0":
+        {"alu_warp_inst": 56014758, "fma_warp_inst": 44574310, "dram_bytes": 8481792},
+    "resident-pairwise:6e3adf86db1b26bb:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 44113663, "fma_warp_inst": None, "dram_bytes": 8467200},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).

@@ -50,6 +50,12 @@ __device__ __forceinline__ uint32_t nibble_range(int m_lo, int m_hi) {
 // 72 M against 43 M warp instructions per MCS at L = 8192 before, 67 M against 54 M after).
 static __constant__ uint32_t c_one = 1u;
 
+// Threshold table entry at a byte offset (the unit cores build offsets, 4 x the index, in their
+// packed lanes, which saves the scaling of each address).
+__device__ __forceinline__ uint32_t table_at(const uint32_t *__restrict__ s_table, uint32_t off) {
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(s_table) + off);
+}
+
 struct UnitCtx {
     uint64_t k;
     uint32_t a;       // sublattice row index of the unit
@@ -101,13 +107,13 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     // bytes: even sites (m = 0, 2, 4, 6) and odd sites; A = s_x*26 + S_x <= 51
     const uint32_t Ae = (Px & kLowNib) + (Qx & kLowNib) + 26u * (sx & 0x01010101u);
     const uint32_t Ao = ((Px >> 4) & kLowNib) + ((Qx >> 4) & kLowNib) + 26u * ((sx >> 4) & 0x01010101u);
-    const uint32_t Be = (Py & kLowNib) + (Qy & kLowNib);
-    const uint32_t Bo = ((Py >> 4) & kLowNib) + ((Qy >> 4) & kLowNib);
-    // halfword lanes: table index (s_x*26 + S_x)*26 + S_y <= 1351
-    const uint32_t Ie01 = __byte_perm(Ae, 0u, 0x4140) * 26u + __byte_perm(Be, 0u, 0x4140);  // m = 0, 2
-    const uint32_t Ie23 = __byte_perm(Ae, 0u, 0x4342) * 26u + __byte_perm(Be, 0u, 0x4342);  // m = 4, 6
-    const uint32_t Io01 = __byte_perm(Ao, 0u, 0x4140) * 26u + __byte_perm(Bo, 0u, 0x4140);  // m = 1, 3
-    const uint32_t Io23 = __byte_perm(Ao, 0u, 0x4342) * 26u + __byte_perm(Bo, 0u, 0x4342);  // m = 5, 7
+    const uint32_t Be = ((Py & kLowNib) + (Qy & kLowNib)) * 4u;                 // 4 S_y <= 100
+    const uint32_t Bo = (((Py >> 4) & kLowNib) + ((Qy >> 4) & kLowNib)) * 4u;
+    // halfword lanes: byte offset of the table entry, 4 ((s_x*26 + S_x)*26 + S_y) <= 5404
+    const uint32_t Ie01 = __byte_perm(Ae, 0u, 0x4140) * 104u + __byte_perm(Be, 0u, 0x4140);  // m = 0, 2
+    const uint32_t Ie23 = __byte_perm(Ae, 0u, 0x4342) * 104u + __byte_perm(Be, 0u, 0x4342);  // m = 4, 6
+    const uint32_t Io01 = __byte_perm(Ao, 0u, 0x4140) * 104u + __byte_perm(Bo, 0u, 0x4140);  // m = 1, 3
+    const uint32_t Io23 = __byte_perm(Ao, 0u, 0x4342) * 104u + __byte_perm(Bo, 0u, 0x4342);  // m = 5, 7
 
     // adoption draws: call 2gw serves sites 0..3, call 2gw+1 sites 4..7. Both calls run
     // (interleaved) whenever the word has an active site: the lanes of a warp seldom need the
@@ -118,13 +124,13 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     uint4 u0 = make_uint4(g0, u.a, kl, kh), u1 = make_uint4(g0 + 1u, u.a, kl, kh);
     philox_rk2(u0, u1, rk);
 
+    // every site looks its threshold up (all offsets lie inside the table) and the sites that
+    // are not active are masked out once at the end: cheaper than a predicate per site
     uint32_t flips = 0;
 #define PGG_SITE(M, IREG, HALF, UW)                                                 \
     {                                                                               \
-        const uint32_t bit = 1u << (4 * (M));                                       \
-        const uint32_t idx = (IREG >> (16 * (HALF))) & 0xFFFFu;                     \
-        const uint32_t t = (active & bit) ? s_table[idx] : 0u;                      \
-        flips |= ((UW) < t) ? bit : 0u;                                             \
+        const uint32_t off = (IREG >> (16 * (HALF))) & 0xFFFFu;                     \
+        flips |= ((UW) < table_at(s_table, off)) ? 1u << (4 * (M)) : 0u;            \
     }
     PGG_SITE(0, Ie01, 0, u0.x)
     PGG_SITE(1, Io01, 0, u0.y)
@@ -135,7 +141,7 @@ __device__ __forceinline__ uint32_t unit_flips(const uint32_t (&wl)[7], const ui
     PGG_SITE(6, Ie23, 1, u1.z)
     PGG_SITE(7, Io23, 1, u1.w)
 #undef PGG_SITE
-    return flips;
+    return flips & active;
 }
 
 // The pairwise game (Section VI): every player plays a 2x2 game with each of its four
@@ -173,9 +179,9 @@ __device__ __forceinline__ uint32_t unit_flips_pair(const uint32_t (&wl)[7], con
 #undef PGG_Y
     const uint32_t lo_n = lo_b * 15u, hi_n = hi_b * 15u;
     const uint32_t ny = mux(hi_n, mux(lo_n, ne, nw), mux(lo_n, ns, nn));
-    // bytes: even sites (m = 0, 2, 4, 6) and odd sites; index 25 s_x + 5 n_x + n_y <= 49
-    const uint32_t Ie = 25u * (sx & 0x01010101u) + 5u * (nx & kLowNib) + (ny & kLowNib);
-    const uint32_t Io = 25u * ((sx >> 4) & 0x01010101u) + 5u * ((nx >> 4) & kLowNib) + ((ny >> 4) & kLowNib);
+    // bytes: even sites (m = 0, 2, 4, 6) and odd sites; byte offset 4 (25 s_x + 5 n_x + n_y) <= 196
+    const uint32_t Ie = 100u * (sx & 0x01010101u) + 20u * (nx & kLowNib) + 4u * (ny & kLowNib);
+    const uint32_t Io = 100u * ((sx >> 4) & 0x01010101u) + 20u * ((nx >> 4) & kLowNib) + 4u * ((ny >> 4) & kLowNib);
 
     // adoption draws: both calls whenever the word has an active site (as in unit_flips)
     const uint32_t g0 = 2u * static_cast<uint32_t>(u.gw);
@@ -186,10 +192,8 @@ __device__ __forceinline__ uint32_t unit_flips_pair(const uint32_t (&wl)[7], con
     uint32_t flips = 0;
 #define PGG_SITE(M, IREG, BYTE, UW)                                                 \
     {                                                                               \
-        const uint32_t bit = 1u << (4 * (M));                                       \
-        const uint32_t idx = (IREG >> (8 * (BYTE))) & 0xFFu;                        \
-        const uint32_t t = (active & bit) ? s_table[idx] : 0u;                      \
-        flips |= ((UW) < t) ? bit : 0u;                                             \
+        const uint32_t off = (IREG >> (8 * (BYTE))) & 0xFFu;                        \
+        flips |= ((UW) < table_at(s_table, off)) ? 1u << (4 * (M)) : 0u;            \
     }
     PGG_SITE(0, Ie, 0, u0.x)
     PGG_SITE(1, Io, 0, u0.y)
@@ -200,7 +204,7 @@ __device__ __forceinline__ uint32_t unit_flips_pair(const uint32_t (&wl)[7], con
     PGG_SITE(6, Ie, 3, u1.z)
     PGG_SITE(7, Io, 3, u1.w)
 #undef PGG_SITE
-    return flips;
+    return flips & active;
 }
 
 template <int OJ, int GAME>
