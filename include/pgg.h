@@ -37,11 +37,14 @@
  *   - Every function returns a pgg_status; no C++ exception crosses the ABI. On failure
  *     pgg_last_error() returns a message for the calling thread.
  *   - A context owns all device memory it allocates; host and device buffers passed
- *     in are borrowed for the duration of the call only.
+ *     in are borrowed for the duration of the call only (pgg_stage_lattice_packed: until
+ *     its copy has completed, as stated there).
  *   - Work is enqueued on the CUDA stream given to pgg_create (borrowed, not owned;
  *     NULL = the legacy default stream). Calls are asynchronous on that stream unless
  *     stated otherwise. A context must not be used from two threads at once.
- *   - Lattices cross the ABI as L*L bytes, row-major, 1 = cooperator, 0 = defector.
+ *   - Lattices cross the ABI as L*L bytes, row-major, 1 = cooperator, 0 = defector, or,
+ *     in the *_packed calls, as L rows of L/32 uint32 words (bit b of word w = column
+ *     32w + b).
  */
 #ifndef PGG_H
 #define PGG_H
