@@ -136,7 +136,7 @@ int pgg_set_game(pgg_ctx *ctx, int game, const double payoff[4]);
 int pgg_get_game(const pgg_ctx *ctx, int *game, double *payoff_out);
 
 /* Initial condition of Section III: every site independently C with probability p
- * (p = 0.5: "equal probability"), drawn from the Philox stream of `seed`; sets the step
+ * (p = 0.5: the even start of Section III), drawn from the Philox stream of `seed`; sets the step
  * counter to 0 and the seed used by later steps. 0 <= p <= 1. */
 int pgg_seed(pgg_ctx *ctx, uint64_t seed, double p);
 

@@ -23,9 +23,12 @@ Parity status of each function (what pins it; the tests live in ``tests/``):
                        VI: one line less than the group game), a brute-force
                        replay of whole steps, equal payoffs = coin flips,
                        absorbing states, order independence, schedule agreement.
-  offset / dir / u     no external pin: they are the stream-layout convention
-                       shared by contract with the GPU library (parity unpinned
-                       beyond uniformity checks).
+  offset / dir / u,    the stream layout is a convention (the paper names no
+  init                 generator), so no outside value fixes it: the pins write the
+                       documented counter layout out over the known-answer-pinned
+                       Philox primitive and require these draws to follow it, then
+                       replay whole group-game and pairwise steps from it with
+                       brute-force payoffs; uniformity checks besides.
 """
 from __future__ import annotations
 

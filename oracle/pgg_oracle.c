@@ -21,7 +21,7 @@
  *     site whose (row mod 4, column mod 4) equals an offset drawn for that step;
  *     16 steps are one full Monte Carlo step (MCS, Section III: L^2 elementary
  *     updates). Concurrent sites are at Manhattan distance >= 4, so the radius-3
- *     read set of one update (Section IV, Fig. 3: "three lines outward") never
+ *     read set of one update (Section IV, Fig. 3: a halo three rows deep) never
  *     contains another update's site; the sites of one step are therefore updated
  *     here one after the other, in row-major order (or reversed, for the
  *     order-independence pin).

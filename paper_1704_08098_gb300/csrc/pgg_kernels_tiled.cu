@@ -3,8 +3,8 @@
 // One CTA owns a tile of tile_y x tile_x sites. It stages the tile plus a halo in shared
 // memory as bit rows (one bit per site, for both lattice layouts), applies `steps`
 // consecutive sublattice steps there, and writes the interior back. An update reads the
-// Manhattan ball of radius R = 3 around its site (Section IV, Fig. 3: "three lines
-// outward"; R = 2 for the pairwise game, one line less, Section VI), so after step j
+// Manhattan ball of radius R = 3 around its site (Section IV, Fig. 3: the halo is
+// three rows deep; R = 2 for the pairwise game, one line less, Section VI), so after step j
 // (0-based) of k only the sites within R (k - 1 - j) of the interior are still needed and
 // still correct; the halo is therefore R k sites wide and the updated region shrinks by R
 // per step. Every random draw is keyed by global (step, site), so the

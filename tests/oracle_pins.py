@@ -260,6 +260,99 @@ def pin_stream_uniformity(o):
 
 
 # --------------------------------------------------------------------------- #
+# The random-stream layout                                                      #
+# --------------------------------------------------------------------------- #
+# The paper names no generator, so the counter layout of the draws is this library's convention
+# and no outside value fixes it. These pins write the documented layout out over the Philox
+# primitive (itself pinned by the published known-answer vectors), require the oracle's draws to
+# follow it, and replay whole sublattice steps from it with brute-force payoffs.
+M32 = 0xFFFFFFFF
+
+
+def _key(seed: int):
+    return (seed & M32, (seed >> 32) & M32)
+
+
+def layout_offset(o, seed: int, k: int) -> int:
+    """Offset of step k: call (m_lo, m_hi, 0, tag 2), m = k >> 5; nibble k & 7 of word (k >> 3) & 3."""
+    m = k >> 5
+    w = o.philox((m & M32, m >> 32, 0, 2 << 24), _key(seed))
+    return (int(w[(k >> 3) & 3]) >> (4 * (k & 7))) & 15
+
+
+def layout_dir(o, seed: int, k: int, a: int, b: int) -> int:
+    """Direction of sublattice site (a, b) at step k: call (b >> 6, a, k_lo, k_hi | tag 3);
+    2-bit field b & 15 of word (b >> 4) & 3."""
+    w = o.philox((b >> 6, a, k & M32, (k >> 32) | (3 << 24)), _key(seed))
+    return (int(w[(b >> 4) & 3]) >> (2 * (b & 15))) & 3
+
+
+def layout_u(o, seed: int, k: int, a: int, b: int) -> int:
+    """Adoption draw of sublattice site (a, b) at step k: word b & 3 of call (b >> 2, a, k_lo, k_hi | tag 4)."""
+    w = o.philox((b >> 2, a, k & M32, (k >> 32) | (4 << 24)), _key(seed))
+    return int(w[b & 3])
+
+
+def layout_init(o, L: int, seed: int, p: float) -> np.ndarray:
+    """Initial state: site x = i L + j is C iff word x & 3 of call (q_lo, q_hi, 0, tag 1),
+    q = x >> 2, is below floor(p 2^32) (2^32 for p = 1)."""
+    thr = TWO32 if p >= 1.0 else int(math.floor(p * TWO32))
+    lat = np.zeros((L, L), dtype=np.uint8)
+    for x in range(L * L):
+        q = x >> 2
+        w = o.philox((q & M32, q >> 32, 0, 1 << 24), _key(seed))
+        lat.flat[x] = 1 if int(w[x & 3]) < thr else 0
+    return lat
+
+
+def pin_stream_layout(o):
+    rng = np.random.default_rng(2024)
+    seeds = [0, 1, 42, (1 << 32) + 5, (1 << 64) - 1] + [int(x) for x in rng.integers(0, 1 << 63, 3)]
+    steps = [0, 1, 7, 8, 31, 32, 33, 255, M32, (1 << 32) + 17, (1 << 56) - 1] + \
+        [int(x) for x in rng.integers(0, 1 << 56, 4)]
+    sites = [(0, 0), (0, 3), (0, 4), (0, 15), (0, 16), (0, 63), (0, 64), (5, 17), (1023, 4095)] + \
+        [(int(a), int(b)) for a, b in rng.integers(0, 2048, (6, 2))]
+    for seed in seeds:
+        for k in steps:
+            assert o.offset(seed, k) == layout_offset(o, seed, k), (seed, k)
+            for a, b in sites:
+                assert o.dir(seed, k, a, b) == layout_dir(o, seed, k, a, b), (seed, k, a, b)
+                assert o.u(seed, k, a, b) == layout_u(o, seed, k, a, b), (seed, k, a, b)
+    for L, seed, p in ((8, 3, 0.5), (12, (1 << 40) + 1, 0.3), (4, 9, 1.0), (4, 9, 0.0), (16, 77, 0.5)):
+        assert np.array_equal(o.init(L, seed, p), layout_init(o, L, seed, p)), (L, seed, p)
+
+
+def replay_step(o, lat: np.ndarray, r: float, K: float, seed: int, k: int) -> np.ndarray:
+    """One group-game sublattice step written out from the stream layout, with payoffs from
+    brute_force_payoffs (all sites of a step are independent)."""
+    L = lat.shape[0]
+    NB = [(0, 1), (0, -1), (1, 0), (-1, 0)]
+    pays, _ = brute_force_payoffs(lat, r)
+    out = lat.copy()
+    off = layout_offset(o, seed, k)
+    for a in range(L // 4):
+        for b in range(L // 4):
+            i, j = 4 * a + (off >> 2), 4 * b + (off & 3)
+            d = layout_dir(o, seed, k, a, b)
+            yi, yj = (i + NB[d][0]) % L, (j + NB[d][1]) % L
+            if lat[i, j] == lat[yi, yj]:
+                continue
+            t = o.threshold(float(pays[i, j]), float(pays[yi, yj]), K)
+            if layout_u(o, seed, k, a, b) < t:
+                out[i, j] = lat[yi, yj]
+    return out
+
+
+def pin_step_brute_force(o):
+    for L, r, K, seed in ((8, 3.8, 0.5, 5), (12, 4.4, 0.2, 6), (8, 2.9, 1.5, (1 << 33) + 7)):
+        lat = layout_init(o, L, seed, 0.5)
+        for k in range(24):
+            want = replay_step(o, lat, r, K, seed, k)
+            o.sublattice_step(lat, r, K, seed, k)
+            assert np.array_equal(lat, want), (L, r, k)
+
+
+# --------------------------------------------------------------------------- #
 # Statistical pins against the paper's reported physics (Section V)            #
 # --------------------------------------------------------------------------- #
 def stationary_density(o, L, r, K, seed, n_mcs, window, classic=False, threads=4):
@@ -418,22 +511,22 @@ def pin_pair_read_set(o):
 
 
 def replay_pair_step(o, lat: np.ndarray, pay, K: float, seed: int, k: int) -> np.ndarray:
-    """One sublattice step written out from the stream definitions, with bond-by-bond
+    """One pairwise sublattice step written out from the stream layout, with bond-by-bond
     payoffs from brute_force_pair_payoffs (all sites of a step are independent)."""
     L = lat.shape[0]
     NB = [(0, 1), (0, -1), (1, 0), (-1, 0)]
     pays, _ = brute_force_pair_payoffs(lat, pay)
     out = lat.copy()
-    off = o.offset(seed, k)
+    off = layout_offset(o, seed, k)
     for a in range(L // 4):
         for b in range(L // 4):
             i, j = 4 * a + (off >> 2), 4 * b + (off & 3)
-            d = o.dir(seed, k, a, b)
+            d = layout_dir(o, seed, k, a, b)
             yi, yj = (i + NB[d][0]) % L, (j + NB[d][1]) % L
             if lat[i, j] == lat[yi, yj]:
                 continue
             t = o.threshold(float(pays[i, j]), float(pays[yi, yj]), K)
-            if o.u(seed, k, a, b) < t:
+            if layout_u(o, seed, k, a, b) < t:
                 out[i, j] = lat[yi, yj]
     return out
 
@@ -507,6 +600,7 @@ FAST_PINS = [pin_philox_kat, pin_payoff_hand_worked, pin_payoff_brute_force,
              pin_payoff_closed_forms, pin_fermi_threshold, pin_adoption_comparator,
              pin_init_density, pin_absorbing_states, pin_counts_match_lattice,
              pin_schedule_coverage, pin_order_independence, pin_stream_uniformity,
+             pin_stream_layout, pin_step_brute_force,
              pin_payoff_consistency_during_run, pin_pair_payoff_hand_worked, pin_pair_brute_force,
              pin_pair_closed_forms, pin_pair_read_set, pin_pair_step_brute_force,
              pin_pair_equal_payoffs, pin_pair_absorbing_and_order,

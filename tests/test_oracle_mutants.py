@@ -31,6 +31,12 @@ MUTANTS = {
     "philox_word_swap": ("uint32_t n1 = lo1;", "uint32_t n1 = lo0;"),
     "total_misses_one_group": ("for (int d = 0; d < 4; ++d)\n        S += oracle_group_cooperators",
                                "for (int d = 0; d < 3; ++d)\n        S += oracle_group_cooperators"),
+    # the random-stream layout
+    "dir_field_width": ("return (int)((word >> (2 * (b & 15))) & 3u);", "return (int)((word >> (2 * (b & 7))) & 3u);"),
+    "dir_word_index": ("uint32_t word = w[(b >> 4) & 3];", "uint32_t word = w[(b >> 3) & 3];"),
+    "u_word_index": ("    return w[b & 3];", "    return w[(b + 1) & 3];"),
+    "offset_nibble": ("return (int)((word >> (4 * (k & 7))) & 15u);", "return (int)((word >> (4 * (k & 3))) & 15u);"),
+    "u_counter_row": ("philox_seeded(seed, b >> 2, a, (uint32_t)k,", "philox_seeded(seed, b >> 2, a + 1, (uint32_t)k,"),
     # the pairwise game (Section VI)
     "pair_sucker_temptation_swapped": ("return s_other ? pay[0] : pay[1];", "return s_other ? pay[0] : pay[2];"),
     "pair_total_complement_5": ("(double)(4 - n) * b;", "(double)(5 - n) * b;"),
