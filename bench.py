@@ -289,6 +289,15 @@ def cpu_baseline(args, budget_s=12.0):
                       f"({n * L * L} updates, {el:.1f} s, OpenMP over the sites of a step)"}
 
 
+def workload_config(args) -> dict:
+    """The workload keys both arms report (the same lattice, dynamics and random stream)."""
+    L = args.L
+    return {"workload": f"L={L} {args.layout} {game_text(args)}, Bernoulli(0.5) start, "
+                        f"seed {args.seed}+rank; one step = 1 MCS = {L * L} site updates",
+            "L": L, "layout": args.layout, "game": args.game, "r": args.r, "K": args.K,
+            "payoff": args.payoff if args.game == "pairwise" else None}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -313,10 +322,9 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": f"L={L} {game_text(args)}, Bernoulli(0.5) "
-                               f"start, seed {args.seed}; one step = 1 MCS", "L": L,
-                   "layout": "u8 (oracle)", "game": args.game, "r": args.r, "K": args.K,
-                   "payoff": args.payoff if args.game == "pairwise" else None},
+        "config": {**workload_config(args),
+                   "implementation": "the CPU oracle (uint8 lattice in host memory, OpenMP over "
+                                     "the sites of a step); results identical to the GPU arm's"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} timed MCS after {args.warmup} warm-up MCS"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -497,11 +505,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "u1" if args.layout == "bitpack" else "u8", "data": "synthetic",
-        "config": {"workload": f"L={L} {args.layout} {game_text(args)}, "
-                               f"Bernoulli(0.5) start, seed {args.seed}+rank; one step = 1 MCS "
-                               f"= {L * L} site updates",
-                   "L": L, "layout": args.layout, "game": args.game, "r": args.r, "K": args.K,
-                   "payoff": args.payoff if args.game == "pairwise" else None,
+        "config": {**workload_config(args),
                    "schedule": sched, "autotuned": tuned,
                    "l2": "flushed between timed steps (256 MiB write, "
                                               "excluded by the per-step CUDA events)",
