@@ -218,7 +218,10 @@ int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int
 int pgg_get_threshold_table(const pgg_ctx *ctx, uint32_t *host_out);
 
 /* Device pointer of the lattice (layout as created) and its size in bytes, for callers
- * that hand the lattice to their own kernels on the same stream. */
+ * that hand the lattice to their own kernels on the same stream. The context may move its
+ * lattice between two buffers (fused tiled schedules alternate them; an applied staged upload
+ * of a bit-packed context takes over the staging buffer), so query the pointer again after any
+ * call that steps or replaces the lattice. */
 int pgg_lattice_device_ptr(pgg_ctx *ctx, void **dev_ptr, uint64_t *bytes);
 
 /* Allocation-free variant of pgg_step_mcs, for callers that cannot allocate device memory

@@ -140,7 +140,7 @@ struct pgg_ctx {
     cudaStream_t copy_stream = nullptr;
     uint32_t *stage_d[2] = {nullptr, nullptr};
     cudaEvent_t stage_ready[2] = {nullptr, nullptr};  // the copy into stage_d[b] has completed
-    cudaEvent_t stage_free[2] = {nullptr, nullptr};   // the context stream has read stage_d[b]
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};   // the context stream no longer uses stage_d[b]
     int stage_next = 0;        // buffer the next pgg_stage_lattice_packed fills
     int stage_pending = -1;    // buffer holding a staged lattice not yet applied, or -1
     uint64_t stage_step = 0;   // step counter that comes with the staged lattice
@@ -252,18 +252,23 @@ int ensure_stage(pgg_ctx *c) {
 }
 
 // Make a staged lattice the context's lattice, in stream order: the context stream waits for
-// its copy, moves it into the lattice (unpacking it for a uint8 lattice) and releases the
-// buffer for a later stage call. Every entry point that reads or writes the lattice or the
-// step counter calls this first.
+// its copy; a bit-packed context then takes the staged buffer as its lattice and hands its old
+// lattice buffer to the stage slot (no copy), a uint8 context unpacks the staged words into its
+// lattice. The event recorded after that frees the slot's buffer for a later stage call once all
+// work queued so far (which may still read the old lattice) has run. Every entry point that reads
+// or writes the lattice or the step counter calls this first.
 int apply_stage(pgg_ctx *c) {
     const int b = c->stage_pending;
     if (b < 0) return PGG_OK;
     c->stage_pending = -1;
     PGG_CUDA(cudaStreamWaitEvent(c->stream, c->stage_ready[b], 0));
-    if (c->layout == PGG_BITPACK)
-        PGG_CUDA(cudaMemcpyAsync(c->lat, c->stage_d[b], c->lat_bytes, cudaMemcpyDeviceToDevice, c->stream));
-    else
+    if (c->layout == PGG_BITPACK) {
+        void *old = c->lat;
+        c->lat = c->stage_d[b];
+        c->stage_d[b] = static_cast<uint32_t *>(old);
+    } else {
         PGG_CUDA(pgg::launch_unpack(c->stage_d[b], static_cast<uint8_t *>(c->lat), c->L, c->stream));
+    }
     PGG_CUDA(cudaEventRecord(c->stage_free[b], c->stream));
     c->step = c->stage_step;
     c->running_valid = false;
