@@ -382,6 +382,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+    lat.set_kernel_timing(True)  # events around each step-kernel launch (the dominant kernel)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(args.steps):
@@ -400,17 +401,20 @@ def main():
         clocks = fine
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), world)
+    kernel_ms, kernel_launches = lat.kernel_time()
+    lat.set_kernel_timing(False)
     value = job_value(float(L) * L, args.steps, world, total_ms)
 
-    # dominant kernel: the step kernel, 16 / k launches per MCS; its launch duration is the
-    # MCS time / launches (includes launch gaps, so it understates the kernel's own rate)
+    # dominant kernel: the step kernel, 16 / k launches per MCS; its average launch duration from
+    # the library's CUDA events around each launch on the launching stream
     k = sched["steps_per_launch"]
     launches_per_mcs = 16 // k
+    assert kernel_launches == launches_per_mcs * args.steps, (kernel_launches, launches_per_mcs)
     # other kernels of ours per MCS: the pack and unpack around a resident call on a uint8
     # lattice, the count of the simple kernel
     extra_launches_per_mcs = (2 if sched["kernel"] == "resident" and args.layout == "u8" else 0) + \
         (1 if sched["kernel"] == "simple" else 0)
-    launch_s = (total_ms / args.steps) / launches_per_mcs / 1e3
+    launch_s = kernel_ms / kernel_launches / 1e3
     updates_per_launch = L * L / 16.0 * k
     pk, pk_kind = peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -444,7 +448,11 @@ def main():
                                  "kernel source yet"}
     roofline.update({"kernel": f"{sched['kernel']} (k={k}, tile {sched['tile_x']}x"
                                f"{sched['tile_y']})", "launch_ms": launch_s * 1e3,
-                     "ncu_key": key, "hbm_model": hbm_model})
+                     "ncu_key": key, "hbm_model": hbm_model,
+                     "launch_timing": "CUDA events recorded by the library around each launch "
+                                      "of the step kernel on its stream, averaged over the timed "
+                                      f"region ({kernel_launches} launches; "
+                                      f"{kernel_ms / (sum(step_ms) or 1.0):.3f} of the step time)"})
 
     # end to end through the public API with host buffers: every step uploads its input lattice
     # from pinned memory (in its bit-packed host form, L*L/8 bytes, for either device layout),

@@ -208,6 +208,15 @@ int pgg_autotune(pgg_ctx *ctx, int n_mcs, int *kernel, int *steps_per_launch, in
  * for testing the failure path. */
 int pgg_set_spin_limit(pgg_ctx *ctx, unsigned int limit);
 
+/* Kernel timing, for measurement: with enable != 0 the context records a CUDA event pair on its
+ * stream around every launch of its step kernel (resident, direct, tiled or simple; not the
+ * conversions, counts or copies around it) from then on, dropping earlier records; enable == 0
+ * stops and releases the events. Both synchronise the stream. pgg_kernel_time synchronises the
+ * stream and returns the summed duration of the recorded launches in milliseconds and their
+ * number (either pointer may be NULL). */
+int pgg_set_kernel_timing(pgg_ctx *ctx, int enable);
+int pgg_kernel_time(pgg_ctx *ctx, double *ms_total, int64_t *launches);
+
 /* The schedule pgg_step_mcs will use (after AUTO resolution). Any pointer may be NULL. */
 int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int *tile_x,
                      int *tile_y);

@@ -144,6 +144,10 @@ struct pgg_ctx {
     int stage_next = 0;        // buffer the next pgg_stage_lattice_packed fills
     int stage_pending = -1;    // buffer holding a staged lattice not yet applied, or -1
     uint64_t stage_step = 0;   // step counter that comes with the staged lattice
+    // kernel timing (pgg_set_kernel_timing): an event pair around every step-kernel launch
+    bool timing = false;
+    std::vector<cudaEvent_t> tev_start, tev_stop;
+    size_t tev_used = 0;
 };
 
 namespace {
@@ -273,6 +277,40 @@ int apply_stage(pgg_ctx *c) {
     c->step = c->stage_step;
     c->running_valid = false;
     return PGG_OK;
+}
+
+// Event before a step-kernel launch when kernel timing is on (pgg_set_kernel_timing).
+int timing_start(pgg_ctx *c) {
+    if (!c->timing) return PGG_OK;
+    if (c->tev_used == c->tev_start.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        if (e != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            return fail(PGG_ERR_CUDA, "kernel timing: cudaEventCreate: %s", cudaGetErrorString(e));
+        }
+        c->tev_start.push_back(a);
+        c->tev_stop.push_back(b);
+    }
+    PGG_CUDA(cudaEventRecord(c->tev_start[c->tev_used], c->stream));
+    return PGG_OK;
+}
+
+// Event after that launch.
+int timing_stop(pgg_ctx *c) {
+    if (!c->timing) return PGG_OK;
+    PGG_CUDA(cudaEventRecord(c->tev_stop[c->tev_used], c->stream));
+    ++c->tev_used;
+    return PGG_OK;
+}
+
+void timing_release(pgg_ctx *c) {
+    for (cudaEvent_t e : c->tev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tev_stop) cudaEventDestroy(e);
+    c->tev_start.clear();
+    c->tev_stop.clear();
+    c->tev_used = 0;
 }
 
 // Report (and clear) a bounded wait that ran out in an earlier resident launch.
@@ -513,7 +551,9 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             a.reset_ctr = c->ctr_launches == 0;
             a.ctr_base = c->ctr_launches << 21;
             ++c->ctr_launches;
+            if (int rc_t = timing_start(c)) return rc_t;
             PGG_CUDA(pgg::launch_resident(a, c->stream));
+            if (int rc_t = timing_stop(c)) return rc_t;
             c->step += 16ull * static_cast<uint64_t>(a.n_mcs);
         }
         if (c->layout == PGG_U8)
@@ -539,15 +579,19 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     for (int64_t m = 0; m < n_mcs; ++m) {
         if (s.kernel == PGG_KERNEL_DIRECT) {
             for (int j = 0; j < 16; ++j) {
+                if (int rc_t = timing_start(c)) return rc_t;
                 PGG_CUDA(pgg::launch_step_direct(c->game, static_cast<uint32_t *>(c->lat), c->L, c->seed, c->step, c->table_d,
                                                  c->running_d, c->status_d, s.tile_x, s.tile_y, c->stream));
+                if (int rc_t = timing_stop(c)) return rc_t;
                 ++c->step;
             }
             PGG_CUDA(cudaMemcpyAsync(c->counts_d + m, c->running_d, sizeof(unsigned long long),
                                      cudaMemcpyDeviceToDevice, c->stream));
         } else if (s.kernel == PGG_KERNEL_SIMPLE) {
             for (int j = 0; j < 16; ++j) {
+                if (int rc_t = timing_start(c)) return rc_t;
                 PGG_CUDA(pgg::launch_step_simple(c->layout, c->game, c->lat, c->L, c->seed, c->step, c->table_d, c->stream));
+                if (int rc_t = timing_stop(c)) return rc_t;
                 ++c->step;
             }
             PGG_CUDA(pgg::launch_popcount(c->lat, c->lat_bytes, c->counts_d + m, c->stream));
@@ -567,7 +611,9 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
                 a.table = c->table_d;
                 a.count_out = (j + s.k == 16) ? c->counts_d + m : nullptr;
                 a.status = c->status_d;
+                if (int rc_t = timing_start(c)) return rc_t;
                 PGG_CUDA(pgg::launch_step_tiled(a, c->stream));
+                if (int rc_t = timing_stop(c)) return rc_t;
                 if (s.k > 1) {
                     void *t = c->lat;
                     c->lat = c->lat_alt;
@@ -765,6 +811,36 @@ int pgg_set_spin_limit(pgg_ctx *c, unsigned int limit) {
     return PGG_OK;
 }
 
+int pgg_set_kernel_timing(pgg_ctx *c, int enable) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_set_kernel_timing: NULL context");
+    PGG_CUDA(cudaSetDevice(c->device));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));  // no recorded event is still pending
+    if (enable) {
+        c->tev_used = 0;
+    } else {
+        timing_release(c);
+    }
+    c->timing = enable != 0;
+    return PGG_OK;
+}
+
+int pgg_kernel_time(pgg_ctx *c, double *ms_total, int64_t *launches) {
+    g_last_error.clear();
+    if (!c) return fail(PGG_ERR_ARG, "pgg_kernel_time: NULL context");
+    PGG_CUDA(cudaSetDevice(c->device));
+    PGG_CUDA(cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (size_t i = 0; i < c->tev_used; ++i) {
+        float ms = 0.0f;
+        PGG_CUDA(cudaEventElapsedTime(&ms, c->tev_start[i], c->tev_stop[i]));
+        total += ms;
+    }
+    if (ms_total) *ms_total = total;
+    if (launches) *launches = static_cast<int64_t>(c->tev_used);
+    return PGG_OK;
+}
+
 int pgg_get_schedule(const pgg_ctx *c, int *kernel, int *steps_per_launch, int *tile_x, int *tile_y) {
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_get_schedule: NULL context");
@@ -908,6 +984,7 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->ctr_d) cudaFree(c->ctr_d);
     if (c->status_d) cudaFree(c->status_d);
     if (c->status_h) cudaFreeHost(c->status_h);
+    timing_release(c);
     if (c->counts_h) cudaFreeHost(c->counts_h);
     delete c;
 }

@@ -58,6 +58,8 @@ def _declare(lib):
         "pgg_get_lattice_packed": (ctypes.c_int, [_vp, _u32p, _u64p]),
         "pgg_set_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
         "pgg_stage_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
+        "pgg_set_kernel_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "pgg_kernel_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]),
         "pgg_get_schedule": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
@@ -289,6 +291,16 @@ class Lattice:
         kern = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         self._check(self.lib.pgg_set_schedule(self._h, kern, int(steps_per_launch), int(tile_x),
                                         int(tile_y)), "pgg_set_schedule")
+
+    def set_kernel_timing(self, enable: bool) -> None:
+        """pgg_set_kernel_timing: CUDA events around every step-kernel launch from now on."""
+        self._check(self.lib.pgg_set_kernel_timing(self._h, int(bool(enable))), "pgg_set_kernel_timing")
+
+    def kernel_time(self) -> tuple[float, int]:
+        """(summed milliseconds, launches) of the step-kernel launches recorded so far."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.lib.pgg_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)), "pgg_kernel_time")
+        return float(ms.value), int(n.value)
 
     def set_spin_limit(self, limit: int) -> None:
         self._check(self.lib.pgg_set_spin_limit(self._h, int(limit)), "pgg_set_spin_limit")

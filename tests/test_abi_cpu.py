@@ -56,6 +56,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.pgg_set_lattice_packed(None, None, 0) == pgg.PGG_ERR_ARG
     assert lib.pgg_get_lattice_packed(None, None, None) == pgg.PGG_ERR_ARG
     assert lib.pgg_stage_lattice_packed(None, None, 0) == pgg.PGG_ERR_ARG
+    assert lib.pgg_set_kernel_timing(None, 1) == pgg.PGG_ERR_ARG
+    assert lib.pgg_kernel_time(None, None, None) == pgg.PGG_ERR_ARG
     lib.pgg_destroy(None)
     assert lib.pgg_version().decode().startswith("pgg-gb300")
 

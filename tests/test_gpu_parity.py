@@ -457,6 +457,31 @@ def test_set_params_mid_run(o, pgg, kernel):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("kernel,k,per_mcs", [("resident", 16, 1), ("direct", 1, 16), ("tiled", 4, 4),
+                                               ("simple", 1, 16)])
+def test_kernel_timing_counts_step_launches(o, pgg, kernel, k, per_mcs):
+    """pgg_set_kernel_timing / pgg_kernel_time: one event pair per step-kernel launch, a positive
+    duration no longer than the calls took, and results unchanged."""
+    import time
+    L = 256
+    ref = o.init(L, 4, 0.5)
+    want = o.run(ref, 3.9, 0.5, 4, 0, 5, threads=THREADS)
+    with pgg.Lattice(L, 3.9, 0.5, layout="bitpack") as lat:
+        lat.set_schedule(kernel, k)
+        lat.seed(4, 0.5)
+        c1 = lat.step_mcs(2)
+        lat.set_kernel_timing(True)
+        t0 = time.perf_counter()
+        c2 = lat.step_mcs(3)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        ms, n = lat.kernel_time()
+        lat.set_kernel_timing(False)
+        assert lat.kernel_time() == (0.0, 0)
+        got, _ = lat.get()
+    assert n == 3 * per_mcs and 0.0 < ms <= wall_ms
+    assert np.array_equal(np.concatenate([c1, c2]), want) and np.array_equal(got, ref)
+
+
 def test_resident_many_launches(o, pgg):
     """2100 one-MCS calls on one context: the neighbour counters carry a per-launch base that
     wraps (and is reset) after 2047 launches; the trajectory must not notice."""
