@@ -457,11 +457,12 @@ def test_set_params_mid_run(o, pgg, kernel):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("kernel,k,per_mcs", [("resident", 16, 1), ("direct", 1, 16), ("tiled", 4, 4),
-                                               ("simple", 1, 16)])
-def test_kernel_timing_counts_step_launches(o, pgg, kernel, k, per_mcs):
+# step-kernel launches of one 3-MCS call: the resident kernel runs a whole call in one launch
+@pytest.mark.parametrize("kernel,k,launches", [("resident", 16, 1), ("direct", 1, 48), ("tiled", 4, 12),
+                                               ("simple", 1, 48)])
+def test_kernel_timing_counts_step_launches(o, pgg, kernel, k, launches):
     """pgg_set_kernel_timing / pgg_kernel_time: one event pair per step-kernel launch, a positive
-    duration no longer than the calls took, and results unchanged."""
+    duration no longer than the call took, and results unchanged."""
     import time
     L = 256
     ref = o.init(L, 4, 0.5)
@@ -478,7 +479,7 @@ def test_kernel_timing_counts_step_launches(o, pgg, kernel, k, per_mcs):
         lat.set_kernel_timing(False)
         assert lat.kernel_time() == (0.0, 0)
         got, _ = lat.get()
-    assert n == 3 * per_mcs and 0.0 < ms <= wall_ms
+    assert n == launches and 0.0 < ms <= wall_ms
     assert np.array_equal(np.concatenate([c1, c2]), want) and np.array_equal(got, ref)
 
 
