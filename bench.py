@@ -382,7 +382,6 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    lat.set_kernel_timing(True)  # events around each step-kernel launch (the dominant kernel)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(args.steps):
@@ -401,12 +400,20 @@ def main():
         clocks = fine
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), world)
+    # the step kernel alone, in an untimed pass of as many MCS: events around each of its launches
+    # (recorded by the library; they lengthen a step by a few microseconds, so the timed region
+    # above runs without them)
+    lat.set_kernel_timing(True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        lat.advance(1)
     kernel_ms, kernel_launches = lat.kernel_time()
     lat.set_kernel_timing(False)
     value = job_value(float(L) * L, args.steps, world, total_ms)
 
-    # dominant kernel: the step kernel, 16 / k launches per MCS; its average launch duration from
-    # the library's CUDA events around each launch on the launching stream
+    # dominant kernel: the step kernel, 16 / k launches per MCS; its launch duration is the timed
+    # MCS time / launches (launch gaps and the counts memset included, so it understates the
+    # kernel's own rate a little; the event-timed pass gives the kernel alone)
     k = sched["steps_per_launch"]
     launches_per_mcs = 16 // k
     assert kernel_launches == launches_per_mcs * args.steps, (kernel_launches, launches_per_mcs)
@@ -414,7 +421,7 @@ def main():
     # lattice, the count of the simple kernel
     extra_launches_per_mcs = (2 if sched["kernel"] == "resident" and args.layout == "u8" else 0) + \
         (1 if sched["kernel"] == "simple" else 0)
-    launch_s = kernel_ms / kernel_launches / 1e3
+    launch_s = (total_ms / args.steps) / launches_per_mcs / 1e3
     updates_per_launch = L * L / 16.0 * k
     pk, pk_kind = peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -449,10 +456,12 @@ def main():
     roofline.update({"kernel": f"{sched['kernel']} (k={k}, tile {sched['tile_x']}x"
                                f"{sched['tile_y']})", "launch_ms": launch_s * 1e3,
                      "ncu_key": key, "hbm_model": hbm_model,
-                     "launch_timing": "CUDA events recorded by the library around each launch "
-                                      "of the step kernel on its stream, averaged over the timed "
-                                      f"region ({kernel_launches} launches; "
-                                      f"{kernel_ms / (sum(step_ms) or 1.0):.3f} of the step time)"})
+                     "launch_timing": "timed MCS time / launches per MCS (CUDA events on the "
+                                      "launching stream, L2 flushed between steps)",
+                     "kernel_events_ms": kernel_ms / kernel_launches,
+                     "kernel_events": "the step kernel alone: CUDA events recorded by the library "
+                                      f"around each of {kernel_launches} launches in an untimed "
+                                      "pass after the timed region"})
 
     # end to end through the public API with host buffers: every step uploads its input lattice
     # from pinned memory (in its bit-packed host form, L*L/8 bytes, for either device layout),
