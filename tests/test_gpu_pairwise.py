@@ -151,6 +151,21 @@ def test_pair_full_size_default_schedule(o, pgg, layout):
     assert np.array_equal(got_lat, want_lat)
 
 
+def test_pair_long_run_L8192_one_mcs_per_call(o, pgg):
+    """The pairwise benchmark's configuration (L = 8192 bit-packed, weak prisoner's dilemma,
+    K = 0.1, the resident kernel, one call per MCS) for its first 40 MCS."""
+    L, n = 8192, 40
+    want_lat, want_counts = run_oracle(o, L, WEAK_PD, 0.1, 3, n)
+    with pgg.Lattice(L, 4.0, 0.1, layout="bitpack") as lat:
+        lat.set_game("pairwise", WEAK_PD)
+        lat.set_schedule("resident")
+        lat.seed(3)
+        got_counts = np.concatenate([lat.step_mcs(1) for _ in range(n)])
+        got_lat, _ = lat.get()
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
 def test_pair_structured_inputs_and_game_switching(o, pgg):
     """A clustered start, switching game and kernel between calls: each call plays the game
     set at the time, on the state the previous call left."""

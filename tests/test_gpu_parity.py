@@ -331,6 +331,23 @@ def test_full_size_against_oracle(o, pgg, L, n_mcs, layout):
     assert np.array_equal(got_lat, want_lat)
 
 
+@pytest.mark.parametrize("L,n_mcs", [(4096, 100), (8192, 50)])
+def test_full_size_long_runs_one_mcs_per_call(o, pgg, L, n_mcs):
+    """Long runs at the benchmark's sizes in its launch configuration (bit-packed, the resident
+    kernel, one call and one launch per MCS): the count after every MCS and the final lattice
+    equal the oracle's (the first 100 MCS at L = 4096 and 50 at L = 8192; the oracle is too slow
+    for the full 2 x 10^4-MCS runs there)."""
+    want_lat, want_counts = run_oracle(o, L, 3.744, 0.5, 7, n_mcs)
+    with pgg.Lattice(L, 3.744, 0.5, layout="bitpack") as lat:
+        lat.set_schedule("resident")
+        lat.seed(7, 0.5)
+        got_counts = np.concatenate([lat.step_mcs(1) for _ in range(n_mcs)])
+        got_lat, step = lat.get()
+    assert step == 16 * n_mcs
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
 DIRECT = {"direct4": dict(kernel="direct", tile_x=4, tile_y=128), "direct8": dict(kernel="direct", tile_x=8, tile_y=64),
           "direct8b256": dict(kernel="direct", tile_x=8, tile_y=256)}
 
