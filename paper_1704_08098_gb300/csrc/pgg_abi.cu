@@ -240,18 +240,48 @@ int ensure_staging(pgg_ctx *c) {
     return PGG_OK;
 }
 
+// Release the overlapped-upload resources (after the copy stream has drained).
+void release_stage(pgg_ctx *c) {
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+        c->copy_stream = nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->stage_d[b]) cudaFree(c->stage_d[b]);
+        if (c->stage_ready[b]) cudaEventDestroy(c->stage_ready[b]);
+        if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
+        c->stage_d[b] = nullptr;
+        c->stage_ready[b] = c->stage_free[b] = nullptr;
+    }
+    c->stage_next = 0;
+    c->stage_pending = -1;
+}
+
+// The copy stream, both staging buffers and their events, all or none (a partial failure
+// releases what was made, so a later call starts afresh).
 int ensure_stage(pgg_ctx *c) {
     if (c->copy_stream) return PGG_OK;
     const size_t bytes = static_cast<size_t>(c->L) * c->L / 8;
     cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) c->copy_stream = nullptr;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-        if ((e = cudaMalloc(&c->stage_d[b], bytes)) != cudaSuccess) break;
-        if ((e = cudaEventCreateWithFlags(&c->stage_ready[b], cudaEventDisableTiming)) != cudaSuccess) break;
-        if ((e = cudaEventCreateWithFlags(&c->stage_free[b], cudaEventDisableTiming)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&c->stage_d[b], bytes)) != cudaSuccess) { c->stage_d[b] = nullptr; break; }
+        if ((e = cudaEventCreateWithFlags(&c->stage_ready[b], cudaEventDisableTiming)) != cudaSuccess) {
+            c->stage_ready[b] = nullptr;
+            break;
+        }
+        if ((e = cudaEventCreateWithFlags(&c->stage_free[b], cudaEventDisableTiming)) != cudaSuccess) {
+            c->stage_free[b] = nullptr;
+            break;
+        }
         e = cudaEventRecord(c->stage_free[b], c->stream);  // both buffers start free
     }
-    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PGG_ERR_OOM : PGG_ERR_CUDA,
-                                      "pgg_stage_lattice_packed: copy stream, buffers or events: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        release_stage(c);
+        return fail(e == cudaErrorMemoryAllocation ? PGG_ERR_OOM : PGG_ERR_CUDA,
+                    "pgg_stage_lattice_packed: copy stream, buffers or events: %s", cudaGetErrorString(e));
+    }
     return PGG_OK;
 }
 
@@ -964,15 +994,7 @@ void pgg_destroy(pgg_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    if (c->copy_stream) {
-        cudaStreamSynchronize(c->copy_stream);
-        cudaStreamDestroy(c->copy_stream);
-    }
-    for (int b = 0; b < 2; ++b) {
-        if (c->stage_d[b]) cudaFree(c->stage_d[b]);
-        if (c->stage_ready[b]) cudaEventDestroy(c->stage_ready[b]);
-        if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
-    }
+    release_stage(c);
     if (c->lat) cudaFree(c->lat);
     if (c->lat_alt) cudaFree(c->lat_alt);
     if (c->table_d) cudaFree(c->table_d);
