@@ -43,7 +43,7 @@ NCU = {
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
     "resident:6e3adf86db1b26bb:bitpack:8192:16:152:0":
         {"alu_warp_inst": 56014758, "fma_warp_inst": 44574310, "dram_bytes": 8481792},
-    # a uint8 context runs the same kernel on a packed copy (counters of that kernel alone)
+    # a uint8 context runs the same kernel, staging and writing back the uint8 lattice itself
     "resident:6e3adf86db1b26bb:u8:8192:16:152:0":
         {"alu_warp_inst": 56014758, "fma_warp_inst": 44574310, "dram_bytes": 8481792},
     "resident-pairwise:6e3adf86db1b26bb:bitpack:8192:16:152:0":
@@ -417,10 +417,8 @@ def main():
     k = sched["steps_per_launch"]
     launches_per_mcs = 16 // k
     assert kernel_launches == launches_per_mcs * args.steps, (kernel_launches, launches_per_mcs)
-    # other kernels of ours per MCS: the pack and unpack around a resident call on a uint8
-    # lattice, the count of the simple kernel
-    extra_launches_per_mcs = (2 if sched["kernel"] == "resident" and args.layout == "u8" else 0) + \
-        (1 if sched["kernel"] == "simple" else 0)
+    # other kernels of ours per MCS: the count of the simple kernel
+    extra_launches_per_mcs = 1 if sched["kernel"] == "simple" else 0
     launch_s = (total_ms / args.steps) / launches_per_mcs / 1e3
     updates_per_launch = L * L / 16.0 * k
     pk, pk_kind = peaks()

@@ -104,8 +104,8 @@ typedef enum {
                               each CTA keeps a band of rows for all MCS and exchanges its 3
                               edge rows with its neighbours between sublattice steps; waits
                               are bounded (a time-out returns PGG_ERR_TIMEOUT at the next
-                              synchronising call). A PGG_U8 lattice is packed into a scratch
-                              bit-packed copy at the start of the call and unpacked at its end */
+                              synchronising call). A PGG_U8 lattice is packed as its bands
+                              are staged and unpacked as they are written back */
 } pgg_kernel;
 
 /* Create a context for one L x L lattice with synergy factor r and noise K (Section III,

@@ -127,7 +127,6 @@ struct pgg_ctx {
     int sms = 0;
     size_t smem_optin = 0;
     uint32_t *mailbox_d = nullptr;
-    uint32_t *packed_d = nullptr;  // bit-packed copy of a uint8 lattice during a resident call
     unsigned int *ctr_d = nullptr;
     unsigned int ctr_launches = 0;  // resident launches since ctr_d was last zeroed
     int *status_d = nullptr;
@@ -549,19 +548,12 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             if (e == cudaSuccess) e = cudaMalloc(&c->ctr_d, sizeof(unsigned int) * bands);
             if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(resident buffers): %s", cudaGetErrorString(e));
         }
-        // the kernel works on the bit-packed form: a uint8 lattice is packed for the call
-        uint32_t *packed = static_cast<uint32_t *>(c->lat);
-        if (c->layout == PGG_U8) {
-            if (!c->packed_d) {
-                cudaError_t e = cudaMalloc(&c->packed_d, static_cast<size_t>(c->L) * c->L / 8);
-                if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(packed copy): %s", cudaGetErrorString(e));
-            }
-            packed = c->packed_d;
-            PGG_CUDA(pgg::launch_pack(static_cast<const uint8_t *>(c->lat), packed, c->L, c->stream));
-        }
+        // the kernel keeps the band bit-packed in shared memory; a uint8 lattice is packed as it is
+        // staged and unpacked as it is written back
         pgg::ResidentArgs a;
         a.game = c->game;
-        a.lat = packed;
+        a.lat = c->layout == PGG_BITPACK ? static_cast<uint32_t *>(c->lat) : nullptr;
+        a.lat8 = c->layout == PGG_U8 ? static_cast<uint8_t *>(c->lat) : nullptr;
         a.L = c->L;
         a.n_bands = bands;
         a.seed = c->seed;
@@ -586,8 +578,6 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             if (int rc_t = timing_stop(c)) return rc_t;
             c->step += 16ull * static_cast<uint64_t>(a.n_mcs);
         }
-        if (c->layout == PGG_U8)
-            PGG_CUDA(pgg::launch_unpack(packed, static_cast<uint8_t *>(c->lat), c->L, c->stream));
         c->running_valid = false;
         PGG_CUDA(cudaGetLastError());
         return coop_per_mcs ? deliver_counts(c, coop_per_mcs, n_mcs) : PGG_OK;
@@ -1002,7 +992,6 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->staging_d) cudaFree(c->staging_d);
     if (c->running_d) cudaFree(c->running_d);
     if (c->mailbox_d) cudaFree(c->mailbox_d);
-    if (c->packed_d) cudaFree(c->packed_d);
     if (c->ctr_d) cudaFree(c->ctr_d);
     if (c->status_d) cudaFree(c->status_d);
     if (c->status_h) cudaFreeHost(c->status_h);

@@ -75,7 +75,8 @@ size_t tiled_smem_bytes(int layout, int game, int steps, int tile_x, int tile_y)
 // one row band per CTA, edge rows exchanged through a mailbox between steps).
 struct ResidentArgs {
     int game;                     // Game (pgg_device.cuh)
-    uint32_t *lat;
+    uint32_t *lat;                // bit-packed lattice, or
+    uint8_t *lat8 = nullptr;      // a uint8 lattice (then lat is unused): packed as it is staged
     int L;
     int n_bands;
     uint64_t seed, k0;

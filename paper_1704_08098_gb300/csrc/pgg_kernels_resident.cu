@@ -25,7 +25,8 @@
 // neighbours and refreshes the halo for the at most two edge rows: the wait overlaps work (the
 // edge rows go to the threads the interior leaves one task short). The count after each MCS is
 // the sum of the bands' population counts. The band is staged with 4-byte cp.async copies and
-// written back once per launch.
+// written back once per launch; a uint8 lattice is packed as its band is staged (two 16-byte
+// loads per word) and unpacked as it is written back, so it needs no conversion launches.
 #include <cuda_runtime.h>
 
 #include "pgg_device.cuh"
@@ -40,7 +41,8 @@ constexpr int kResThreads = kComputeThreads + 32;     // plus one warp that exch
 constexpr int kResMaxUPT = 4;  // words per task at most (a task stays inside one 8-word direction call)
 
 struct ResidentParams {
-    uint32_t *lat;            // global lattice (read at the start, written at the end)
+    uint32_t *lat;            // bit-packed global lattice (read at the start, written at the end)
+    uint8_t *lat8;            // or, when not null, a uint8 lattice (lat unused)
     int L, Lw, n_bands;
     uint64_t seed, k0;
     int n_mcs;
@@ -53,6 +55,25 @@ struct ResidentParams {
     unsigned int spin_limit;
     PhiloxKeys rk;
 };
+
+// Four bytes, each 0 or 1, to four bits (byte i to bit i): the product puts byte i's bit at
+// bit 24 + i, and no two partial products share a bit position, so nothing carries.
+__device__ __forceinline__ uint32_t pack_bytes4(uint32_t x) { return (x * 0x01020408u) >> 24; }
+
+// 32 bytes of a uint8 row (0 or 1 each) to the bit-packed word (byte b to bit b).
+__device__ __forceinline__ uint32_t pack_bytes32(const uint4 &a, const uint4 &b) {
+    return pack_bytes4(a.x) | pack_bytes4(a.y) << 4 | pack_bytes4(a.z) << 8 | pack_bytes4(a.w) << 12 |
+           pack_bytes4(b.x) << 16 | pack_bytes4(b.y) << 20 | pack_bytes4(b.z) << 24 | pack_bytes4(b.w) << 28;
+}
+
+// Four bits to four bytes of 0 or 1 (bit i to byte i): the product puts bit i at bit 8 i, and no
+// two partial products share a bit position.
+__device__ __forceinline__ uint32_t unpack_bits4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+
+__device__ __forceinline__ uint4 unpack_bits16(uint32_t h) {
+    return make_uint4(unpack_bits4(h & 15u), unpack_bits4((h >> 4) & 15u), unpack_bits4((h >> 8) & 15u),
+                      unpack_bits4((h >> 12) & 15u));
+}
 
 __device__ __forceinline__ int band_start(int b, int L, int n) { return static_cast<int>((static_cast<long long>(b) * L) / n); }
 
@@ -259,7 +280,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const uint32_t edge_bytes = static_cast<uint32_t>(edge * sizeof(uint32_t));
     const PhiloxKeys rk = p.rk;
     // bulk copies need 16-byte aligned rows (the same answer in every CTA: all stop together)
-    if ((smem_u32(s_rows) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u) {
+    if ((smem_u32(s_rows) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u ||
+        (reinterpret_cast<uintptr_t>(p.lat8) & 15u) != 0u) {
         if (tid == 0) atomicOr(p.status, 2);
         return;
     }
@@ -276,11 +298,25 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const int scol = swz(col);
     if (row_first < rows_per_pass) {
         int g = wrap_small(r0 - 3 + row_first, L);
-        for (int lr = row_first; lr < nb + 6; lr += rows_per_pass) {
-            if (index_ok(static_cast<long long>(g) * Lw + col, static_cast<long long>(L) * Lw, p.status))
-                copy_async4(&s_rows[lr * Lw + scol], &p.lat[static_cast<size_t>(g) * Lw + col]);
-            g += rows_per_pass;
-            if (g >= L) g -= L;
+        if (p.lat8) {
+            // uint8 lattice: the word's 32 bytes in two 16-byte loads (rows start 256-byte aligned)
+#pragma unroll 4
+            for (int lr = row_first; lr < nb + 6; lr += rows_per_pass) {
+                const size_t off = static_cast<size_t>(g) * L + 32 * static_cast<size_t>(col);
+                if (index_ok(static_cast<long long>(off) + 31, static_cast<long long>(L) * L, p.status)) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(p.lat8 + off);
+                    s_rows[lr * Lw + scol] = pack_bytes32(src[0], src[1]);
+                }
+                g += rows_per_pass;
+                if (g >= L) g -= L;
+            }
+        } else {
+            for (int lr = row_first; lr < nb + 6; lr += rows_per_pass) {
+                if (index_ok(static_cast<long long>(g) * Lw + col, static_cast<long long>(L) * Lw, p.status))
+                    copy_async4(&s_rows[lr * Lw + scol], &p.lat[static_cast<size_t>(g) * Lw + col]);
+                g += rows_per_pass;
+                if (g >= L) g -= L;
+            }
         }
     }
     copy_async_wait_all();
@@ -398,9 +434,21 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     __syncthreads();  // the last bulk store has completed (its issuer waited) before the band is stored
     // store the band (the same column-per-thread walk)
     if (row_first < rows_per_pass) {
-        for (int lr = row_first; lr < nb; lr += rows_per_pass) {
-            if (index_ok(static_cast<long long>(r0 + lr) * Lw + col, static_cast<long long>(L) * Lw, p.status))
-                p.lat[static_cast<size_t>(r0 + lr) * Lw + col] = s_rows[(lr + 3) * Lw + scol];
+        if (p.lat8) {
+            for (int lr = row_first; lr < nb; lr += rows_per_pass) {
+                const size_t off = static_cast<size_t>(r0 + lr) * L + 32 * static_cast<size_t>(col);
+                if (index_ok(static_cast<long long>(off) + 31, static_cast<long long>(L) * L, p.status)) {
+                    const uint32_t w = s_rows[(lr + 3) * Lw + scol];
+                    uint4 *dst = reinterpret_cast<uint4 *>(p.lat8 + off);
+                    dst[0] = unpack_bits16(w & 0xFFFFu);
+                    dst[1] = unpack_bits16(w >> 16);
+                }
+            }
+        } else {
+            for (int lr = row_first; lr < nb; lr += rows_per_pass) {
+                if (index_ok(static_cast<long long>(r0 + lr) * Lw + col, static_cast<long long>(L) * Lw, p.status))
+                    p.lat[static_cast<size_t>(r0 + lr) * Lw + col] = s_rows[(lr + 3) * Lw + scol];
+            }
         }
     }
 }
@@ -426,6 +474,7 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     if (a.n_bands < 1 || a.L % 256 != 0) return cudaErrorInvalidValue;
     ResidentParams p;
     p.lat = a.lat;
+    p.lat8 = a.lat8;
     p.L = a.L;
     p.Lw = a.L / 32;
     p.n_bands = a.n_bands;
