@@ -41,13 +41,13 @@ FALLBACK_HBM_GBS = 6800.0
 NCU = {
     "direct:1385c7b1fc7d18a3:bitpack:8192:1:4:64":
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
-    "resident:6e3adf86db1b26bb:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 56014758, "fma_warp_inst": 44574310, "dram_bytes": 8481792},
+    "resident:59b615d25f4199b1:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 56250783, "fma_warp_inst": 44529750, "dram_bytes": 8485376},
     # a uint8 context runs the same kernel, staging and writing back the uint8 lattice itself
-    "resident:6e3adf86db1b26bb:u8:8192:16:152:0":
-        {"alu_warp_inst": 56014758, "fma_warp_inst": 44574310, "dram_bytes": 8481792},
-    "resident-pairwise:6e3adf86db1b26bb:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 44113663, "fma_warp_inst": None, "dram_bytes": 8467200},
+    "resident:59b615d25f4199b1:u8:8192:16:152:0":
+        {"alu_warp_inst": 58792335, "fma_warp_inst": 46059208, "dram_bytes": 79408640},
+    "resident-pairwise:59b615d25f4199b1:bitpack:8192:16:152:0":
+        {"alu_warp_inst": 44228756, "fma_warp_inst": 29225428, "dram_bytes": 8470784},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
