@@ -70,3 +70,15 @@ def test_product_path_never_imports_the_oracle():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "pgg_oracle" not in text and "liboracle" not in text, path
+
+
+def test_stored_counters_match_the_current_kernel_sources():
+    """bench.py's roofline takes per-launch instruction and DRAM counts from a table keyed by a
+    hash of the kernel's sources (stale counts must not be reported for a changed kernel): the
+    table holds entries for the current resident and direct sources."""
+    import bench
+    for kernel in ("resident", "direct"):
+        h = bench.kernel_source_hash(kernel)
+        assert any(k.split(":")[1] == h and k.split(":")[0].startswith(kernel) for k in bench.NCU), kernel
+    for key, v in bench.NCU.items():
+        assert v["alu_warp_inst"] > 0 and v["dram_bytes"] > 0, key
