@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from paper_1704_08098_gb300 import inputs
+from test_golden_trace import load_trace
 
 pytestmark = pytest.mark.gpu
 
@@ -100,6 +101,7 @@ def test_rho_trace_L64_1000_mcs(o, pgg, layout, sched):
     assert k == 16 * w["n_mcs"]
     assert np.array_equal(got_counts, want_counts)
     assert np.array_equal(got_lat, want_lat)
+    assert np.array_equal(got_counts, load_trace())   # the stored oracle trace
 
 
 @pytest.mark.parametrize("L", [4, 8, 12, 20, 36, 100])
