@@ -82,3 +82,14 @@ def test_stored_counters_match_the_current_kernel_sources():
         assert any(k.split(":")[1] == h and k.split(":")[0].startswith(kernel) for k in bench.NCU), kernel
     for key, v in bench.NCU.items():
         assert v["alu_warp_inst"] > 0 and v["dram_bytes"] > 0, key
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No fallback: with the CUDA library absent the binding raises instead of computing anything."""
+    from paper_1704_08098_gb300 import pgg
+    monkeypatch.setattr(pgg, "_lib", None)
+    monkeypatch.setattr(pgg, "LIB_PATH", os.path.join(os.path.dirname(pgg.LIB_PATH), "absent.so"))
+    with pytest.raises(RuntimeError, match="CUDA library not built"):
+        pgg.load()
+    with pytest.raises(RuntimeError, match="CUDA library not built"):
+        pgg.Lattice(64, 4.0, 0.5)
