@@ -12,8 +12,8 @@ from paper_1704_08098_gb300 import inputs
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rho_trace_L64_counts.txt")
 
 
-def load_trace():
-    with open(GOLDEN) as f:
+def load_trace(path=GOLDEN):
+    with open(path) as f:
         rows = [line for line in f if not line.startswith("#") and line.strip()]
     return np.array([int(x) for x in rows], dtype=np.uint64)
 
@@ -28,3 +28,14 @@ def test_oracle_reproduces_the_stored_trace():
     assert np.array_equal(got, want)
     # the run is neither absorbed nor frozen: the counts move and stay inside (0, L^2)
     assert 0 < int(want.min()) and int(want.max()) < w["L"] ** 2 and len(set(want.tolist())) > 100
+
+
+def test_pairwise_oracle_reproduces_the_stored_trace():
+    path = os.path.join(os.path.dirname(GOLDEN), "pair_trace_L64_counts.txt")
+    want = load_trace(path)
+    assert len(want) == 600
+    o = oracle.Oracle()
+    lat = o.init(64, 1, 0.5)
+    got = o.pair_run(lat, (1.0, 0.0, 1.04, 0.0), 0.1, 1, 0, 600)
+    assert np.array_equal(got, want)
+    assert 0 < int(want.min()) and int(want.max()) < 64 ** 2 and len(set(want.tolist())) > 50
