@@ -226,6 +226,13 @@ int pgg_get_schedule(const pgg_ctx *ctx, int *kernel, int *steps_per_launch, int
  * 2*5*5 entries hold the table indexed (s_x*5 + n_x)*5 + n_y and the rest are zero. */
 int pgg_get_threshold_table(const pgg_ctx *ctx, uint32_t *host_out);
 
+/* The same table built on the host for the given game and parameters, without a context or a
+ * device (the library's own statement of Eq. (3) and the payoff rules, callable anywhere):
+ * game PGG_GAME_GROUP needs r > 0 (payoff ignored, may be NULL), PGG_GAME_PAIRWISE needs the 4
+ * finite payoffs {R, S, T, P} (r ignored); K > 0. host_out receives 2*26*26 uint32 laid out as
+ * above. */
+int pgg_threshold_table(int game, double r, double K, const double payoff[4], uint32_t *host_out);
+
 /* Device pointer of the lattice (layout as created) and its size in bytes, for callers
  * that hand the lattice to their own kernels on the same stream. The context may move its
  * lattice between two buffers (fused tiled schedules alternate them; an applied staged upload

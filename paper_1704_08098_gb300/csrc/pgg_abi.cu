@@ -879,6 +879,23 @@ int pgg_get_threshold_table(const pgg_ctx *c, uint32_t *host_out) {
     return PGG_OK;
 }
 
+int pgg_threshold_table(int game, double r, double K, const double payoff[4], uint32_t *host_out) {
+    g_last_error.clear();
+    if (!host_out) return fail(PGG_ERR_ARG, "pgg_threshold_table: NULL output");
+    if (!(K > 0.0) || !std::isfinite(K)) return fail(PGG_ERR_ARG, "pgg_threshold_table: need K > 0");
+    if (game == PGG_GAME_GROUP) {
+        if (!(r > 0.0) || !std::isfinite(r)) return fail(PGG_ERR_ARG, "pgg_threshold_table: need r > 0");
+        pgg::build_threshold_table(r, K, host_out);
+        return PGG_OK;
+    }
+    if (game != PGG_GAME_PAIRWISE) return fail(PGG_ERR_ARG, "pgg_threshold_table: unknown game %d", game);
+    if (!payoff) return fail(PGG_ERR_ARG, "pgg_threshold_table: the pairwise game needs its payoff matrix");
+    for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(payoff[q])) return fail(PGG_ERR_ARG, "pgg_threshold_table: payoff[%d] is not finite", q);
+    pgg::build_pair_threshold_table(payoff, K, host_out);
+    return PGG_OK;
+}
+
 int pgg_lattice_device_ptr(pgg_ctx *c, void **dev_ptr, uint64_t *bytes) {
     g_last_error.clear();
     if (!c) return fail(PGG_ERR_ARG, "pgg_lattice_device_ptr: NULL context");

@@ -59,6 +59,8 @@ def _declare(lib):
         "pgg_set_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
         "pgg_stage_lattice_packed": (ctypes.c_int, [_vp, _u32p, ctypes.c_uint64]),
         "pgg_set_kernel_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+        "pgg_threshold_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.POINTER(ctypes.c_double), _u32p]),
         "pgg_kernel_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "pgg_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]),
@@ -336,6 +338,20 @@ class Lattice:
         self._check(self.lib.pgg_lattice_device_ptr(self._h, ctypes.byref(p), ctypes.byref(n)),
               "pgg_lattice_device_ptr")
         return int(p.value or 0), int(n.value)
+
+
+def threshold_table(r: float, K: float, game: str = "group", payoff=None) -> np.ndarray:
+    """pgg_threshold_table: the (2, 26, 26) uint32 adoption thresholds built on the host (no
+    device needed); for the pairwise game the first 2*5*5 entries, indexed (s_x*5 + n_x)*5 + n_y."""
+    lib = load()
+    out = np.zeros((2, 26, 26), dtype=np.uint32)
+    pay = None
+    if payoff is not None:
+        pay_arr = (ctypes.c_double * 4)(*[float(x) for x in payoff])
+        pay = ctypes.cast(pay_arr, ctypes.POINTER(ctypes.c_double))
+    check(lib.pgg_threshold_table(GAMES[game], float(r), float(K), pay,
+                                  out.ctypes.data_as(_u32p)), "pgg_threshold_table")
+    return out
 
 
 def step_mcs_noalloc(lattice_in: int, lattice_out: int, L: int, layout, r: float, K: float,

@@ -93,3 +93,39 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
         pgg.load()
     with pytest.raises(RuntimeError, match="CUDA library not built"):
         pgg.Lattice(64, 4.0, 0.5)
+
+
+def test_host_threshold_tables_match_the_oracle():
+    """The library's host-built adoption tables (its own statement of Eq. (3) and the payoff rules,
+    pgg_threshold_table, no device needed) equal the oracle's thresholds entry by entry, for the
+    group game and the pairwise game of Section VI, including the K -> 0 and K -> infinity limits."""
+    import oracle
+    from paper_1704_08098_gb300 import pgg
+    o = oracle.Oracle()
+    for r, K in ((4.0, 0.5), (3.7443, 0.5), (3.98, 0.5), (5.0, 0.1), (4.2, 1e-6), (3.5, 1e6), (2.0, 3.3)):
+        T = pgg.threshold_table(r, K)
+        for sx in (0, 1):
+            for Sx in range(26):
+                for Sy in range(26):
+                    want = o.threshold(o.payoff_total(sx, Sx, r), o.payoff_total(1 - sx, Sy, r), K)
+                    assert int(T[sx, Sx, Sy]) == want, (r, K, sx, Sx, Sy)
+    for pay, K in (((1.0, 0.0, 1.04, 0.0), 0.1), ((1.0, 0.5, 1.5, 0.0), 0.5), ((3.0, -1.0, 5.0, 0.5), 2.0),
+                   ((1.0, 0.0, 1.5, 0.0), 1e-6), ((2.0, 2.0, 2.0, 2.0), 0.4)):
+        T = pgg.threshold_table(4.0, K, "pairwise", pay).reshape(-1)
+        assert not T[50:].any()
+        for sx in (0, 1):
+            for nx in range(5):
+                for ny in range(5):
+                    want = o.threshold(o.pair_payoff_total(sx, nx, pay), o.pair_payoff_total(1 - sx, ny, pay), K)
+                    assert int(T[(sx * 5 + nx) * 5 + ny]) == want, (pay, K, sx, nx, ny)
+
+
+def test_host_threshold_table_argument_checks(lib):
+    from paper_1704_08098_gb300 import pgg
+    out = (ctypes.c_uint32 * (2 * 26 * 26))()
+    assert lib.pgg_threshold_table(pgg.GAME_GROUP, 4.0, 0.5, None, None) == pgg.PGG_ERR_ARG
+    assert lib.pgg_threshold_table(pgg.GAME_GROUP, 4.0, 0.0, None, out) == pgg.PGG_ERR_ARG
+    assert lib.pgg_threshold_table(pgg.GAME_GROUP, -1.0, 0.5, None, out) == pgg.PGG_ERR_ARG
+    assert lib.pgg_threshold_table(pgg.GAME_PAIRWISE, 4.0, 0.5, None, out) == pgg.PGG_ERR_ARG
+    assert lib.pgg_threshold_table(7, 4.0, 0.5, None, out) == pgg.PGG_ERR_ARG
+    assert lib.pgg_threshold_table(pgg.GAME_GROUP, 4.0, 0.5, None, out) == pgg.PGG_OK
