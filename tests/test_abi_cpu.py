@@ -95,7 +95,7 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
         pgg.Lattice(64, 4.0, 0.5)
 
 
-def test_host_threshold_tables_match_the_oracle():
+def test_host_threshold_tables_match_the_oracle(lib):
     """The library's host-built adoption tables (its own statement of Eq. (3) and the payoff rules,
     pgg_threshold_table, no device needed) equal the oracle's thresholds entry by entry, for the
     group game and the pairwise game of Section VI, including the K -> 0 and K -> infinity limits."""
