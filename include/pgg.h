@@ -240,24 +240,30 @@ int pgg_threshold_table(int game, double r, double K, const double payoff[4], ui
  * call that steps or replaces the lattice. */
 int pgg_lattice_device_ptr(pgg_ctx *ctx, void **dev_ptr, uint64_t *bytes);
 
-/* Allocation-free variant of pgg_step_mcs, for callers that cannot allocate device memory
- * (code running inside CUDA-graph capture or a host callback, plug-ins whose host
- * application owns all device memory, services that must not allocate after start-up).
- * The paper has no counterpart; it is a packaging of the fused tiled kernel.
+/* Allocation-free variant of pgg_step_mcs, for callers that cannot allocate device memory:
+ * plug-ins of a host application that hands out all device memory from its own pool (there a
+ * cudaMalloc fails once the pool holds the device, or escapes the application's accounting),
+ * and services that must not allocate after start-up (cudaMalloc may block on the whole device
+ * for an unbounded time). The paper has no counterpart; it is a packaging of the fused tiled
+ * kernel.
  *   lattice_in, lattice_out: device buffers in `layout` (PGG_U8: L*L bytes; PGG_BITPACK:
  *     L*L/8 bytes, see pgg_layout); they may be the same buffer.
  *   Runs n_mcs MCS of the model with (r, K, seed) starting at sublattice step step0
- *   (the state (lattice, seed, step, r, K) is the same as that of a context).
+ *   (the state (lattice, seed, step, r, K) is the same as that of a context); the result is
+ *   the one pgg_step_mcs gives, bit for bit.
  *   coop_per_mcs: NULL or a device buffer of n_mcs uint64 counts; it is cleared and filled.
  *   Requires L % 64 == 0, 64 <= L, and a lattice of at most 4 MiB (L <= 2048 for PGG_U8,
- *   L <= 4096 for PGG_BITPACK); larger sizes return PGG_ERR_ARG with a message.
+ *   L <= 4096 for PGG_BITPACK), and step0 + 16 n_mcs < 2^56; otherwise PGG_ERR_ARG with a
+ *   message.
  * It calls no cudaMalloc, cudaFree or allocating routine: its scratch (a 4 MiB intermediate
- * lattice plus the threshold table) is one fixed device array in the library, held by every
- * GPU that loads the library until the process exits. The first call on a device resolves
- * that array's address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture. All calls share the array: calls that overlap on the GPU (on
- * different streams or devices' contexts sharing it) race and must be serialised by the
- * caller. Asynchronous on cuda_stream. */
+ * lattice plus the threshold table, which reaches the device as a kernel parameter) is one
+ * fixed device array in the library, held by every GPU that loads the library until the
+ * process exits. The first call on a device resolves that array's address
+ * (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ * capture. All calls share the array and each
+ * overwrites what the last one left there: calls that overlap on the GPU (on different streams)
+ * race and must be serialised by the caller. Asynchronous on cuda_stream. Not callable from a
+ * host function enqueued on a stream (cudaLaunchHostFunc), where CUDA calls are not allowed. */
 int pgg_step_mcs_noalloc(const void *lattice_in, void *lattice_out, int L, int layout, double r,
                          double K, uint64_t seed, uint64_t step0, int64_t n_mcs,
                          uint64_t *coop_per_mcs, void *cuda_stream);

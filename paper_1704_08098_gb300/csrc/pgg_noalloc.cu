@@ -1,13 +1,14 @@
 // pgg_noalloc.cu -- pgg_step_mcs_noalloc: the fused tiled step for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA-graph capture or a
-// host callback, plug-ins of a host application that owns all device memory through its
-// own pool, and code that must not allocate after start-up. This entry point takes the
-// caller's input and output lattices and runs the same fused tiled kernel as
-// pgg_step_mcs, with the kernel's scratch -- the intermediate lattice between the two
-// fused launches of each MCS and the adoption threshold table -- in a fixed, file-scope
-// device array instead of memory allocated per context.
+// Some callers of this library cannot call cudaMalloc: plug-ins of a host application that
+// hands out all device memory from its own pool (a cudaMalloc there fails once the pool has
+// taken the device, or escapes the application's accounting), and services that must not
+// allocate after start-up because cudaMalloc can block on the whole device and take an unbounded
+// time. This entry point takes the caller's input and output lattices and runs the same fused
+// tiled kernel as pgg_step_mcs, with the kernel's scratch -- the intermediate lattice between
+// the two fused launches of each MCS and the adoption threshold table -- in a fixed,
+// file-scope device array instead of memory allocated per context.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -35,6 +36,17 @@ unsigned char *g_scratch_dev[kMaxDevices];  // device address of g_noalloc_scrat
 
 // Two fused launches of 8 sublattice steps per MCS; tile chosen to fit any allowed L.
 constexpr int kFuse = 8;
+
+// The threshold table travels to the device as a kernel parameter (5408 bytes, well inside the
+// 32 KB parameter space), so a call needs no host staging buffer and no pageable copy.
+struct TableParam {
+    uint32_t t[pgg::kTableEntries];
+};
+
+__global__ void k_noalloc_table(const __grid_constant__ TableParam p, uint32_t *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < pgg::kTableEntries) dst[i] = p.t[i];
+}
 
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int code, const char *fmt, ...) {
@@ -82,17 +94,19 @@ extern "C" int pgg_step_mcs_noalloc(const void *lattice_in, void *lattice_out, i
                     layout == PGG_U8 ? "uint8" : "bit-packed", L, bytes, kNoallocLatticeBytes, 2048, 4096);
     if (!(r > 0.0) || !(K > 0.0)) return fail(PGG_ERR_ARG, "pgg_step_mcs_noalloc: need r > 0 and K > 0");
     if (n_mcs < 0) return fail(PGG_ERR_ARG, "pgg_step_mcs_noalloc: n_mcs < 0");
-    if (step0 + 16ull * static_cast<uint64_t>(n_mcs) >= (1ull << 56))
+    // step0 + 16 n_mcs < 2^56, tested without forming the sum (which could wrap)
+    constexpr uint64_t kMaxStep = 1ull << 56;
+    if (step0 >= kMaxStep || static_cast<uint64_t>(n_mcs) > (kMaxStep - 1 - step0) / 16)
         return fail(PGG_ERR_ARG, "pgg_step_mcs_noalloc: step counter would pass 2^56");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     unsigned char *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
     uint32_t *table_d = reinterpret_cast<uint32_t *>(scratch + kNoallocTableOffset);
-    uint32_t table_h[pgg::kTableEntries];
-    pgg::build_threshold_table(r, K, table_h);
-    // from pageable memory: the call returns once table_h has been staged
-    cudaError_t e = cudaMemcpyAsync(table_d, table_h, sizeof table_h, cudaMemcpyHostToDevice, stream);
+    TableParam tp;
+    pgg::build_threshold_table(r, K, tp.t);
+    k_noalloc_table<<<(pgg::kTableEntries + 255) / 256, 256, 0, stream>>>(tp, table_d);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && coop_per_mcs && n_mcs > 0)
         e = cudaMemsetAsync(coop_per_mcs, 0, size_t(n_mcs) * sizeof(uint64_t), stream);
     if (e != cudaSuccess) return fail(PGG_ERR_CUDA, "pgg_step_mcs_noalloc: %s", cudaGetErrorString(e));
