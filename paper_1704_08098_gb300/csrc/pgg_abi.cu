@@ -348,6 +348,10 @@ int status_result(pgg_ctx *c, int st) {
         PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
         PGG_CUDA(cudaStreamSynchronize(c->stream));
         c->running_valid = false;
+        if (st & 8)
+            return fail(PGG_ERR_CUDA, "a resident-kernel CTA stopped after a time-out while a halo copy into its "
+                                      "shared memory was still unconfirmed; results on this device are undefined: "
+                                      "destroy the context and reset the device's CUDA context");
         if (st & 4)
             return fail(PGG_ERR_STATE, "an index check of the checked build failed: a kernel computed an address "
                                        "outside its buffer (the access was skipped; the lattice is not a valid state)");
@@ -531,7 +535,8 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     if (n_mcs < 0) return fail(PGG_ERR_ARG, "pgg_step_mcs: n_mcs < 0");
     if (n_mcs == 0) return PGG_OK;
     const uint64_t step_in = c->stage_pending >= 0 ? c->stage_step : c->step;
-    if (step_in + 16ull * static_cast<uint64_t>(n_mcs) >= kMaxStep)
+    // step_in + 16 n_mcs < 2^56 (step_in < 2^56 always), tested without forming the sum
+    if (static_cast<uint64_t>(n_mcs) > (kMaxStep - 1 - step_in) / 16)
         return fail(PGG_ERR_ARG, "pgg_step_mcs: step counter would pass 2^56");
     PGG_CUDA(cudaSetDevice(c->device));
     if (int rc_stage = apply_stage(c)) return rc_stage;

@@ -508,6 +508,10 @@ int pgg_batch_step_mcs(pgg_batch *b, int n_mcs, uint32_t *counts) {
     if (!b) return bfail(PGG_ERR_ARG, "pgg_batch_step_mcs: NULL batch");
     if (n_mcs < 0) return bfail(PGG_ERR_ARG, "pgg_batch_step_mcs: n_mcs < 0");
     if (n_mcs == 0) return PGG_OK;
+    // every replica's step + 16 n_mcs stays below 2^56 (n_mcs < 2^31, so 16 n_mcs cannot wrap)
+    for (int i = 0; i < b->n; ++i)
+        if (b->host_desc[i].step > (1ull << 56) - 1 - 16ull * static_cast<uint64_t>(n_mcs))
+            return bfail(PGG_ERR_ARG, "pgg_batch_step_mcs: replica %d: step counter would pass 2^56", i);
     PGG_BCUDA(cudaSetDevice(b->device));
     if (!b->jobs_valid) {
         int rc = build_jobs(b);
