@@ -89,7 +89,8 @@ struct ResidentArgs {
     bool reset_ctr;               // zero ctr before the launch (first use, or ctr_base wrapped)
     unsigned long long *counts;   // n_mcs counts, zeroed by the caller
     int *status;                  // | 1 a bounded wait ran out, | 2 the alignment check failed, | 4 an index
-                                  // check failed (checked build)
+                                  // check failed (checked build), | 8 a CTA stopped with a halo load
+                                  // possibly in flight (fatal for the device context)
     unsigned int spin_limit;      // polls before a wait gives up
 };
 int resident_bands(int layout, int L, int sms, size_t smem_optin);

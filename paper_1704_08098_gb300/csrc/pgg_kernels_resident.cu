@@ -51,7 +51,8 @@ struct ResidentParams {
     unsigned int *ctr;        // [band] ctr_base + completed steps of this launch
     unsigned int ctr_base;    // above every value an earlier launch left in ctr
     unsigned long long *counts;  // [n_mcs], zeroed before the launch
-    int *status;              // | 1 a wait timed out, | 2 misaligned buffers, | 4 an index check failed (checked build)
+    int *status;              // | 1 a wait timed out, | 2 misaligned buffers, | 4 an index check failed (checked build),
+                              // | 8 a CTA stopped with a halo load possibly still in flight
     unsigned int spin_limit;
     PhiloxKeys rk;
 };
@@ -398,6 +399,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 unsigned int it = 0;
                 while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>((j - 1) & 1)) && ++it < kMbarTries) {
                 }
+                // the halo load was never seen to land: the CTA leaves with a copy into its
+                // shared memory possibly in flight, which the host must treat as fatal
+                if (it >= kMbarTries) atomicOr(p.status, 8);
             }
             return;
         }
