@@ -47,3 +47,37 @@ def test_adam_first_step_closed_form():
     # bias-corrected first moments equal g and second moments g^2: a step of lr * sign(g)
     assert np.allclose(t1, theta - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_forward_hand_worked_sparse_network():
+    """A network with a handful of non-zero weights (all exact in BF16), worked by hand: the
+    first layer multiplies x by W1 (output unit i reads input j through W1[i, j]) and adds b1,
+    the ReLUs cut negative and zero pre-activations, and the sigmoids of z give p and rho."""
+    P = {name: np.zeros(shape) for name, shape in M.SHAPES}
+    P["W1"][0, 0], P["W1"][0, 1], P["b1"][0] = 2.0, 1.0, 0.25
+    P["W1"][1, 0], P["b1"][1] = -1.0, 0.125
+    P["W1"][2, 200], P["b1"][2] = 1.0, -3.5
+    P["W2"][0, 0], P["W2"][0, 2] = 4.0, -1.0
+    P["W2"][1, 1], P["W2"][1, 2], P["b2"][1] = 100.0, 2.0, -2.0
+    P["W2"][5, 0], P["b2"][5] = -8.0, 3.0
+    P["W3"][0, 0], P["W3"][0, 5], P["b3"][0] = 2.0, -3.0, 0.5
+    P["W3"][1, 5] = 0.75
+    theta = np.concatenate([P[name].reshape(-1) for name, _ in M.SHAPES])
+    assert np.array_equal(M.bf16_round(theta.astype(np.float32)), theta)
+    X = np.zeros((2, M.N_IN))
+    X[0, 0], X[0, 1], X[0, 200], X[0, 201] = 0.5, -1.0, 4.0, 0.5
+    X[1, 0], X[1, 200], X[1, 201] = 1.0, 3.5, 0.5
+    f = M.forward(theta, X)
+    # row 0: a1 = (0.25, -0.375, 0.5) -> h1 = (0.25, 0, 0.5); h2_0 = 1 - 0.5, h2_1 = relu(1 - 2) = 0,
+    # h2_5 = -2 + 3; z = (1 - 3 + 0.5, 0.75)
+    # row 1: h1 = (2.25, 0, relu(0) = 0); h2_0 = 9, h2_5 = relu(-15) = 0; z = (18.5, 0)
+    assert np.allclose(f["h1"][:, :3], [[0.25, 0.0, 0.5], [2.25, 0.0, 0.0]], rtol=0, atol=1e-15)
+    assert np.allclose(f["z"], [[-1.5, 0.75], [18.5, 0.0]], rtol=0, atol=1e-15)
+    want_p = np.array([1.0 / (1.0 + np.exp(1.5)), 1.0 / (1.0 + np.exp(-18.5))])
+    want_rho = np.array([1.0 / (1.0 + np.exp(-0.75)), 0.5])
+    assert np.allclose(f["p"], want_p, rtol=1e-15, atol=0) and np.allclose(f["rho"], want_rho, rtol=1e-15, atol=0)
+    assert abs(f["p"][0] - 0.18242552380635635) < 1e-15 and abs(f["rho"][0] - 0.679178699175393) < 1e-15
+    # loss: labels (absorbed, rho, mask) = (1, 0.6, 1) and (0, 0.2, 0)
+    Y = np.array([[1.0, 0.6, 1.0], [0.0, 0.2, 0.0]])
+    want = (-np.log(want_p[0]) - np.log(1.0 - want_p[1]) + (want_rho[0] - 0.6) ** 2) / 2.0
+    assert abs(M.loss(theta, X, Y) - want) < 1e-14
