@@ -101,8 +101,11 @@ typedef enum {
                               a running total */
     PGG_KERNEL_RESIDENT = 4 /* L % 256 == 0 with the bit-packed rows fitting the SMs'
                               shared memory: one cooperative launch per pgg_step_mcs call,
-                              each CTA keeps a band of rows for all MCS and exchanges its 3
-                              edge rows with its neighbours between sublattice steps; waits
+                              each CTA keeps a band of rows for all MCS and exchanges its
+                              R s edge rows with its neighbours every s sublattice steps
+                              (R = 3 group game, 2 pairwise; s = 1, 2 or 4, updating the
+                              halo rows redundantly in between); only the active sites
+                              (s_x != s_y) of a step are updated, gathered per warp; waits
                               are bounded (a time-out returns PGG_ERR_TIMEOUT at the next
                               synchronising call). A PGG_U8 lattice is packed as its bands
                               are staged and unpacked as they are written back */
@@ -190,7 +193,10 @@ int pgg_get_state(const pgg_ctx *ctx, uint64_t *seed_out, uint64_t *step_out);
  * (1, 2, 4, 8 or 16; PGG_KERNEL_TILED only) and the tile size in sites (tile_x a
  * multiple of 64, tile_y a multiple of 4; 0 = default); for PGG_KERNEL_DIRECT tile_x is
  * the number of words per thread (4 or 8) and tile_y the block size (64, 128, 256), 0 =
- * default. PGG_KERNEL_AUTO restores the tuned default. */
+ * default; for PGG_KERNEL_RESIDENT tile_y is the number of sublattice steps between halo
+ * exchanges (1, 2 or 4; 0 = the largest whose halo rows fit) and tile_x is ignored (the
+ * resolved schedule reports the number of bands there). PGG_KERNEL_AUTO restores the tuned
+ * default. */
 int pgg_set_schedule(pgg_ctx *ctx, int kernel, int steps_per_launch, int tile_x, int tile_y);
 
 /* Autotuner: time every applicable schedule (direct words-per-thread x block size, tiled

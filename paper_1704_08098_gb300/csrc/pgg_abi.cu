@@ -191,7 +191,10 @@ Schedule resolve_schedule(const pgg_ctx *c) {
     if (s.kernel == PGG_KERNEL_RESIDENT) {
         s.k = 16;
         s.tile_x = pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin);
-        s.tile_y = 0;
+        // tile_y: sublattice steps per halo exchange (1, 2 or 4), the largest that fits by default
+        const int smax = s.tile_x > 0 ? pgg::resident_max_steps_per_exchange(c->L, s.tile_x, c->smem_optin) : 1;
+        if (s.tile_y != 1 && s.tile_y != 2 && s.tile_y != 4) s.tile_y = smax;
+        if (s.tile_y > smax) s.tile_y = smax;
         return s;
     }
     if (s.kernel == PGG_KERNEL_DIRECT) {
@@ -568,6 +571,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         a.ctr = c->ctr_d;
         a.status = c->status_d;
         a.spin_limit = c->spin_limit;
+        a.steps_per_exchange = s.tile_y;
         // one launch covers at most 1 << 16 MCS
         for (int64_t m0 = 0; m0 < n_mcs; m0 += (1 << 16)) {
             a.n_mcs = static_cast<int>(std::min<int64_t>(n_mcs - m0, 1 << 16));
@@ -790,12 +794,18 @@ int pgg_set_schedule(pgg_ctx *c, int kernel, int steps_per_launch, int tile_x, i
         kernel != PGG_KERNEL_DIRECT && kernel != PGG_KERNEL_RESIDENT)
         return fail(PGG_ERR_ARG, "pgg_set_schedule: unknown kernel %d", kernel);
     if (kernel == PGG_KERNEL_RESIDENT) {
-        if (pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) < 1)
+        const int bands = pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin);
+        if (bands < 1)
             return fail(PGG_ERR_ARG, "pgg_set_schedule: this lattice cannot be resident (L %% 256 == 0, rows within shared memory)");
+        if (tile_y != 0 && tile_y != 1 && tile_y != 2 && tile_y != 4)
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: resident steps per halo exchange (tile_y) must be 1, 2 or 4");
+        const int smax = pgg::resident_max_steps_per_exchange(c->L, bands, c->smem_optin);
+        if (tile_y > smax)
+            return fail(PGG_ERR_ARG, "pgg_set_schedule: %d steps per halo exchange do not fit (at most %d for L = %d)", tile_y, smax, c->L);
         c->kernel = kernel;
         c->k_fuse = 16;
         c->tile_x = 0;
-        c->tile_y = 0;
+        c->tile_y = tile_y;
         return PGG_OK;
     }
     if (kernel == PGG_KERNEL_DIRECT) {
@@ -920,7 +930,10 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
     if (int rc_stage = apply_stage(c)) return rc_stage;
     // candidates
     std::vector<Schedule> cand;
-    if (pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin) > 0) cand.push_back({PGG_KERNEL_RESIDENT, 16, 0, 0});
+    if (const int bands = pgg::resident_bands(c->layout, c->L, c->sms, c->smem_optin)) {
+        const int smax = pgg::resident_max_steps_per_exchange(c->L, bands, c->smem_optin);
+        for (int spe = 1; spe <= smax; spe *= 2) cand.push_back({PGG_KERNEL_RESIDENT, 16, 0, spe});
+    }
     if (pgg::direct_supported(c->layout, c->L))
         for (int upt : {4, 8})
             for (int blk : {64, 128, 256}) cand.push_back({PGG_KERNEL_DIRECT, 1, upt, blk});

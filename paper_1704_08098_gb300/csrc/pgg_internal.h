@@ -72,7 +72,7 @@ cudaError_t launch_step_direct(int game, uint32_t *lat, int L, uint64_t seed, ui
 size_t tiled_smem_bytes(int layout, int game, int steps, int tile_x, int tile_y);
 
 // Whole bit-packed lattice resident in shared memory for n_mcs MCS (one cooperative launch,
-// one row band per CTA, edge rows exchanged through a mailbox between steps).
+// one row band per CTA, edge rows exchanged through a mailbox every steps_per_exchange steps).
 struct ResidentArgs {
     int game;                     // Game (pgg_device.cuh)
     uint32_t *lat;                // bit-packed lattice, or
@@ -92,8 +92,11 @@ struct ResidentArgs {
                                   // check failed (checked build), | 8 a CTA stopped with a halo load
                                   // possibly in flight (fatal for the device context)
     unsigned int spin_limit;      // polls before a wait gives up
+    int steps_per_exchange = 1;   // sublattice steps between halo exchanges: 1, 2 or 4
 };
 int resident_bands(int layout, int L, int sms, size_t smem_optin);
+// Largest steps_per_exchange (4, 2 or 1) whose halo rows fit the shared memory.
+int resident_max_steps_per_exchange(int L, int n_bands, size_t smem_optin);
 size_t resident_mailbox_words(int L, int n_bands);
 cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s);
 

@@ -1,54 +1,73 @@
 // pgg_kernels_resident.cu -- a whole bit-packed lattice resident in shared memory across
 // many MCS: one cooperative launch, each CTA owning a band of rows.
 //
-// CTA b keeps rows [r0, r1) of the lattice plus 3 halo rows above and below in shared memory
-// for the whole call. A sublattice step writes only rows i = oi (mod 4), at least 4 apart, and
-// an update reads rows i-3 .. i+3 (Section IV, Fig. 3), so within a step no CTA needs data a
-// neighbour writes in that step; between steps each CTA publishes its 3 top and 3 bottom band
-// rows to a double-buffered mailbox in global memory, bumps its step counter, and before the
-// edge rows of the next step waits for both neighbours' counters and their rows in its halo.
-// All CTAs are co-resident (cooperative launch). Every wait is bounded: after `spin_limit`
-// polls the CTA sets the status word and stops; its neighbours then time out in turn.
+// CTA b keeps rows [r0, r0 + nb) of the lattice plus H halo rows above and below in shared
+// memory for the whole call. A sublattice step writes only rows i = oi (mod 4), at least 4
+// apart, and an update reads the Manhattan ball of radius R around its site (R = 3 for the
+// group game, Section IV, Fig. 3; R = 2 for the pairwise game of Section VI), so within a
+// step no CTA needs data a neighbour writes in that step.
+//
+// Halo exchange every s steps (s = 1, 2 or 4; H = R s). The CTA updates, at step j of a
+// block of s steps, the sublattice rows of its band and of the R (s - 1 - j) halo rows next to
+// it on each side: the halo rows are its neighbours' band rows, updated redundantly with the
+// same counter-based draws, so after the block the band is exact and only the neighbours'
+// H edge rows must be fetched again. After each block the CTA publishes its top and bottom H
+// band rows to a double-buffered mailbox in global memory and bumps its block counter; before
+// the rows that read the halo in the first step of the next block it waits for both
+// neighbours' counters and their rows in its halo. All CTAs are co-resident (cooperative
+// launch). Every wait is bounded: after `spin_limit` polls the CTA sets the status word and
+// stops; its neighbours then time out in turn.
 //
 // The exchange runs beside the computation: one extra warp per CTA polls the neighbours'
 // counters, fetches their edge rows into the halo with TMA bulk copies (cp.async.bulk,
-// completion on an mbarrier) and, after each step, bulk-stores the band's own edge rows and
-// releases its counter, while the 16 compute warps update the interior rows; the compute
-// warps wait on the mbarrier only before the edge rows.
+// completion on an mbarrier) and, after each block, bulk-stores the band's own edge rows and
+// releases its counter, while the 16 compute warps update the rows that do not read the halo;
+// the compute warps wait on the mbarrier only before the rows that do.
 //
-// The pairwise game (Section VI) runs the same way with its radius-2 update (its halo rows
-// beyond the second are exchanged but never read).
+// Work within a step: most sites of a sublattice step cannot change, because an update with
+// s_x = s_y is a no-op (Eq. (3) only matters when the strategies differ) and needs no adoption
+// draw (the stream is counter based). Each warp therefore scans words of its sublattice rows
+// (8 sites per 32-column word, the direction draws of 8 words from one Philox call), finds the
+// active sites (s_x != s_y for the drawn neighbour y), and appends them to a ring in shared
+// memory; whenever the ring holds 32 entries, the warp updates them, one site per lane: the
+// group counts S_x and S_y from the 7 x 7 neighbourhood of x (population counts of masked
+// bits), the threshold of Eq. (3) from the host-built table, the adoption draw, and an atomic
+// XOR of the site's bit when it adopts. So the costly part runs at full warp width on active
+// sites only. Updates of one step touch disjoint sites and read only bits no other update of
+// the step changes, so they run in place in any order.
 //
-// Per step the work is the direct kernel's: tasks of one sublattice row and 1-4 words, the shared
-// update core of pgg_unit.cuh, in place in shared memory. A step first updates the band's
-// interior sublattice rows, whose reads stay inside the band, and only then waits for the
-// neighbours and refreshes the halo for the at most two edge rows: the wait overlaps work (the
-// edge rows go to the threads the interior leaves one task short). The count after each MCS is
-// the sum of the bands' population counts. The band is staged with 4-byte cp.async copies and
-// written back once per launch; a uint8 lattice is packed as its band is staged (two 16-byte
-// loads per word) and unpacked as it is written back, so it needs no conversion launches.
+// The count after each MCS is the sum of the bands' population counts. The band is staged
+// with 4-byte cp.async copies and written back once per launch; a uint8 lattice is packed as
+// its band is staged (two 16-byte loads per word) and unpacked as it is written back, so it
+// needs no conversion launches.
 #include <cuda_runtime.h>
 
 #include "pgg_device.cuh"
 #include "pgg_internal.h"
-#include "pgg_unit.cuh"
 
 namespace pgg {
 namespace {
 
-constexpr int kComputeThreads = 512;                 // warps that update the band
-constexpr int kResThreads = kComputeThreads + 32;     // plus one warp that exchanges halos
-constexpr int kResMaxUPT = 4;  // words per task at most (a task stays inside one 8-word direction call)
+constexpr int kComputeThreads = 512;                  // warps that update the band
+constexpr int kComputeWarps = kComputeThreads / 32;
+constexpr int kResThreads = kComputeThreads + 32;      // plus one warp that exchanges halos
+constexpr int kMaxStepsPerExchange = 4;
+constexpr int kMaxHalo = 3 * kMaxStepsPerExchange;    // halo rows per side at most
+constexpr int kMaxLocalRows = 128;                     // band + halo rows (7 bits of a word entry)
+constexpr int kMaxRowWords = 512;                      // words per row (9 bits of a word entry)
+
+constexpr uint32_t kNib = 0x11111111u;
 
 struct ResidentParams {
     uint32_t *lat;            // bit-packed global lattice (read at the start, written at the end)
     uint8_t *lat8;            // or, when not null, a uint8 lattice (lat unused)
     int L, Lw, n_bands;
+    int s, H;                 // sublattice steps per halo exchange, halo rows per side (R s)
     uint64_t seed, k0;
     int n_mcs;
     const uint32_t *table;
-    uint32_t *mailbox;        // [band][parity][top/bottom][3 rows][Lw]
-    unsigned int *ctr;        // [band] ctr_base + completed steps of this launch
+    uint32_t *mailbox;        // [band][parity][top/bottom][H rows][Lw]
+    unsigned int *ctr;        // [band] ctr_base + blocks published in this launch
     unsigned int ctr_base;    // above every value an earlier launch left in ctr
     unsigned long long *counts;  // [n_mcs], zeroed before the launch
     int *status;              // | 1 a wait timed out, | 2 misaligned buffers, | 4 an index check failed (checked build),
@@ -76,11 +95,17 @@ __device__ __forceinline__ uint4 unpack_bits16(uint32_t h) {
                       unpack_bits4((h >> 12) & 15u));
 }
 
+// Periodic wrap of an index that may be a few periods outside [0, m).
+__device__ __forceinline__ int wrap_small(int v, int m) {
+    while (v < 0) v += m;
+    while (v >= m) v -= m;
+    return v;
+}
+
 __device__ __forceinline__ int band_start(int b, int L, int n) { return static_cast<int>((static_cast<long long>(b) * L) / n); }
 
-// Word w of a band row lives at (w ^ ((w >> 5) & 7)): the 32 lanes of a warp, which start
-// tasks u = 1, 2 or 4 words apart (words u c, c = 0..31), then hit 32 different banks (for
-// u = 4: bank 4 (c mod 8) + c / 8; for u = 2: 2c, or 2c - 31 for c >= 16).
+// Word w of a band row lives at (w ^ ((w >> 5) & 7)): lanes that read words 1, 2, 4 or 8 apart
+// (words u c, c = 0..31) then hit 32 different banks.
 __device__ __forceinline__ int swz(int w) { return w ^ ((w >> 5) & 7); }
 
 __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
@@ -93,112 +118,326 @@ __device__ __forceinline__ void store_release(unsigned int *p, unsigned int v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Sublattice rows of the band (global rows r in [r0, r0 + nb) with r = oi (mod 4)), split
-// into the interior ones, whose reads (rows r-R .. r+R, R the game's read radius) stay inside
-// the band, and the at most two edge ones that read halo rows.
-struct BandRows {
-    int first, n_srows, in_lo, in_hi;  // interior = sublattice rows in_lo .. in_hi - 1
+// The 32 columns starting D columns to the right (D < 0: left) of the word whose left, centre
+// and right neighbours are l, c, r.
+template <int D>
+__device__ __forceinline__ uint32_t window(uint32_t l, uint32_t c, uint32_t r) {
+    static_assert(D >= -4 && D <= 4, "window shift out of range");
+    if constexpr (D == 0) return c;
+    else if constexpr (D > 0) return __funnelshift_r(c, r, D);
+    else return __funnelshift_l(l, c, -D);
+}
+
+__device__ __forceinline__ uint32_t mux(uint32_t sel, uint32_t if0, uint32_t if1) { return (if0 & ~sel) | (if1 & sel); }
+
+// --- the 7 x 7 neighbourhood of a site as 49 bits -------------------------------------------
+// Bit 7 r + t holds the site at (row offset r - 3, column offset t - 3); the site itself is bit
+// 24. Relative to a centre at bit 24, the group count sum of Section III, S = sum of the 5
+// group counts of the groups the centre belongs to (Fig. 1), weighs the centre 5 times, its 4
+// nearest neighbours and 4 diagonal neighbours twice, and the 4 sites two steps away along the
+// axes once (a neighbour w of z lies in z's own group and in w's; a diagonal site in the groups
+// of the two neighbours it shares with z; an axis site at distance 2 in the group of the
+// neighbour between them).
+constexpr uint32_t kOnesLo = (1u << 10) | (1u << 22) | (1u << 26);   // (-2, 0), (0, -2), (0, +2)
+constexpr uint32_t kOnesHi = 1u << (38 - 32);                         // (+2, 0)
+constexpr uint32_t kTwosLo = (1u << 16) | (1u << 17) | (1u << 18) | (1u << 23) | (1u << 25) | (1u << 30) | (1u << 31);
+constexpr uint32_t kTwosHi = 1u << (32 - 32);                         // (+1, +1)
+// the 4 nearest neighbours alone (the pairwise game's cooperating neighbours, Section VI)
+constexpr uint32_t kNearLo = (1u << 17) | (1u << 23) | (1u << 25) | (1u << 31);
+
+struct Ctx {
+    uint32_t *rows;                       // band + halo rows (local row lr = global row r0 - H + lr)
+    const uint32_t *__restrict__ table;
+    int L, Lw, r0, H;
+    uint32_t kl, kh_dir, kh_u;            // step index words with the direction / adoption tags
+    const PhiloxKeys *rk;
+    int cpr;                              // 64-word chunks per row
+    uint32_t cmagic;                      // ceil(2^16 / cpr): floor(k / cpr) = (k cmagic) >> 16 for small k
+    long long n_words;                    // words of band + halo rows (checked build)
+    int *status;
 };
 
+// The adoption decision of one active site: entry = local row << 18 | column << 2 | direction
+// code. Returns the bit to flip (0: no adoption) and sets `word` to the index of its word in
+// the band rows.
 template <int GAME>
-__device__ __forceinline__ BandRows band_rows(int r0, int nb, int oi) {
-    constexpr int R = kReadRadius<GAME>;
-    BandRows b;
-    b.first = r0 + ((oi - r0) & 3);
-    b.n_srows = b.first < r0 + nb ? (r0 + nb - b.first + 3) >> 2 : 0;
-    if (b.n_srows == 0) {
-        b.in_lo = b.in_hi = 0;
-        return b;
+__device__ __forceinline__ uint32_t site_flip(const Ctx &cx, uint32_t e, int &word) {
+    const int d = static_cast<int>(e & 3u);
+    const int j = static_cast<int>((e >> 2) & 0xFFFFu);
+    const int lr = static_cast<int>(e >> 18);
+    int i = cx.r0 - cx.H + lr;
+    if (i < 0) i += cx.L;
+    else if (i >= cx.L) i -= cx.L;
+    // adoption draw of sublattice site (a, b) = (i >> 2, j >> 2): word b & 3 of the call at b >> 2
+    uint4 u4 = make_uint4(static_cast<uint32_t>(j >> 4), static_cast<uint32_t>(i >> 2), cx.kl, cx.kh_u);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) philox_round(u4, cx.rk->k0[r], cx.rk->k1[r]);
+    // columns j - 3 .. j + 3 of rows lr - 3 .. lr + 3, from the two words holding them
+    const int c0 = j >= 3 ? j - 3 : j - 3 + cx.L;
+    const int wa = c0 >> 5, wb = wa + 1 == cx.Lw ? 0 : wa + 1, sh = c0 & 31;
+    constexpr int q0 = 3 - kReadRadius<GAME>;  // the rows the game reads: q0 .. 6 - q0
+    const uint32_t *pa = cx.rows + swz(wa) + (lr - 3 + q0) * cx.Lw;
+    const uint32_t *pb = cx.rows + swz(wb) + (lr - 3 + q0) * cx.Lw;
+    uint32_t v[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const long long ra = static_cast<long long>(lr - 3 + q) * cx.Lw;
+        v[q] = (q >= q0 && q <= 6 - q0 && index_ok(ra + swz(wa), cx.n_words, cx.status) &&
+                index_ok(ra + swz(wb), cx.n_words, cx.status))
+                   ? (__funnelshift_r(pa[(q - q0) * cx.Lw], pb[(q - q0) * cx.Lw], sh) & 0x7Fu)
+                   : 0u;
     }
-    const int last = b.first + 4 * (b.n_srows - 1);
-    b.in_lo = b.first - R < r0 ? 1 : 0;
-    b.in_hi = last + R >= r0 + nb ? b.n_srows - 1 : b.n_srows;
-    if (b.in_hi < b.in_lo) b.in_hi = b.in_lo;  // one sublattice row that is an edge row at both ends
-    return b;
-}
-
-// Words per task of the interior phase: 4 when that still gives every thread a task, else
-// fewer, so that small phases spread over all warps instead of a few long tasks.
-__device__ __forceinline__ int interior_task_words(int words) {
-    return words >= kResMaxUPT * kComputeThreads ? kResMaxUPT : (words >= 2 * kComputeThreads ? 2 : 1);
-}
-
-// Update the interior sublattice rows of the band (edge = false) or its edge rows (edge = true:
-// row 0 when in_lo = 1, row n_srows - 1 when in_hi < n_srows; never the same row twice, since
-// in_hi >= in_lo). Rows of one sublattice step are 4 apart and an update reads 3 rows either
-// side, so the two calls touch disjoint sites and need no barrier between them.
-//
-// The interior tasks go to threads 0, 1, ... in turn, so when their number n_int is not a
-// multiple of the thread count, threads f = n_int mod T and up have one task fewer. The edge
-// tasks are dealt to those threads first (task e to thread f + e, wrapping), with as few words
-// per task as still fit them: the edge rows then fill the gap of the last interior round instead
-// of forming a round of their own.
-template <int OJ, int GAME>
-__device__ __forceinline__ void resident_step(uint32_t *s_rows, const uint32_t *__restrict__ s_table,
-                                              const PhiloxKeys &rk, int Lw, int r0, int nb, const BandRows &br,
-                                              bool edge, uint64_t k, int *status) {
-    const long long n_local = static_cast<long long>(nb + 6) * Lw;  // words of band + halo
-    // edge: selected row q is 0 or n_srows - 1 (edge_top: whether row 0 is one of them)
-    const bool edge_top = br.in_lo != 0, edge_bot = br.in_hi < br.n_srows;
-    const int n_rows_sel = edge ? static_cast<int>(edge_top) + static_cast<int>(edge_bot) : br.in_hi - br.in_lo;
-    const int words = n_rows_sel * Lw;
-    int upt, shift = 0;
-    if (edge) {
-        const int int_words = (br.in_hi - br.in_lo) * Lw;
-        const int f = (int_words / interior_task_words(int_words)) % kComputeThreads;
-        const int free_threads = f ? kComputeThreads - f : kComputeThreads;
-        upt = words <= free_threads ? 1 : (words <= 2 * free_threads ? 2 : kResMaxUPT);
-        shift = f;
+    const uint32_t lo = v[0] | v[1] << 7 | v[2] << 14 | v[3] << 21 | v[4] << 28;
+    const uint32_t hi = v[4] >> 4 | v[5] << 3 | v[6] << 10;
+    const uint32_t sx = (v[3] >> 3) & 1u;
+    // the same bits centred on y: shifted right for y to the right (+1) or below (+7), left otherwise
+    const uint32_t rs = d == 0 ? 1u : (d == 2 ? 7u : 0u);
+    const uint32_t ls = d == 1 ? 1u : (d == 3 ? 7u : 0u);
+    uint32_t ylo = __funnelshift_r(lo, hi, rs), yhi = hi >> rs;
+    yhi = __funnelshift_l(ylo, yhi, ls);
+    ylo <<= ls;
+    uint32_t idx;
+    if constexpr (GAME == kPairGame) {
+        const uint32_t nx = __popc(lo & kNearLo), ny = __popc(ylo & kNearLo);
+        idx = (sx * 5u + nx) * 5u + ny;
     } else {
-        upt = interior_task_words(words);
+        const uint32_t Sx = __popc(lo & kOnesLo) + __popc(hi & kOnesHi) +
+                            2u * (__popc(lo & kTwosLo) + __popc(hi & kTwosHi)) + 5u * sx;
+        const uint32_t Sy = __popc(ylo & kOnesLo) + __popc(yhi & kOnesHi) +
+                            2u * (__popc(ylo & kTwosLo) + __popc(yhi & kTwosHi)) + 5u * (1u - sx);
+        idx = (sx * 26u + Sx) * 26u + Sy;
     }
-    const int runs = Lw / upt;
-    const int n_tasks = n_rows_sel * runs;
-    const uint32_t kl = static_cast<uint32_t>(k), kh = static_cast<uint32_t>(k >> 32) | kTagDir;
-    int t0 = static_cast<int>(threadIdx.x) - shift;
-    if (t0 < 0) t0 += kComputeThreads;
-    for (int t = t0; t < n_tasks; t += kComputeThreads) {
-        const int q_sel = t / runs;
-        const int sr = edge ? ((q_sel == 0 && edge_top) ? 0 : br.n_srows - 1) : br.in_lo + q_sel;
-        const int c = t - q_sel * runs;
-        const int i = br.first + 4 * sr;         // global row
-        const int lr = i - r0 + 3;               // local row (3 halo rows above the band)
-        const uint32_t *row0 = s_rows + (lr - 3) * Lw;
-        const int w0 = upt * c;
-        const int wprev = w0 == 0 ? Lw - 1 : w0 - 1;
-        uint32_t wl[7], wc[7], wr[7];
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const long long base = static_cast<long long>(lr - 3 + q) * Lw;
-            wl[q] = reads_row<GAME>(q) && index_ok(base + swz(wprev), n_local, status) ? row0[q * Lw + swz(wprev)] : 0u;
-            wc[q] = reads_row<GAME>(q) && index_ok(base + swz(w0), n_local, status) ? row0[q * Lw + swz(w0)] : 0u;
-        }
-        const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(i >> 2), kl, kh), rk);
-        UnitCtx u;
-        u.k = k;
-        u.a = static_cast<uint32_t>(i >> 2);
-        u.msk = kNib;
-#pragma unroll 1
-        for (int w = w0; w < w0 + upt; ++w) {
-            const int wn = w + 1 == Lw ? 0 : w + 1;
-#pragma unroll
-            for (int q = 0; q < 7; ++q)
-                wr[q] = reads_row<GAME>(q) && index_ok(static_cast<long long>(lr - 3 + q) * Lw + swz(wn), n_local, status)
-                            ? row0[q * Lw + swz(wn)]
-                            : 0u;
-            u.gw = w;
-            u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
-            uint32_t sx;
-            const uint32_t flips = game_flips<OJ, GAME>(wl, wc, wr, u, rk, s_table, sx);
-            // writes stay in the band's own rows (local rows 3 .. nb + 2)
-            if (flips && index_ok(lr - 3, nb, status)) s_rows[lr * Lw + swz(w)] = wc[3] ^ (flips << OJ);
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                wl[q] = wc[q];
-                wc[q] = wr[q];
+    const uint32_t t = index_ok(idx, kTableEntries, cx.status) ? cx.table[idx] : 0u;
+    const int bw = (j >> 2) & 3;
+    const uint32_t u = bw == 0 ? u4.x : bw == 1 ? u4.y : bw == 2 ? u4.z : u4.w;
+    word = lr * cx.Lw + swz(j >> 5);
+    return u < t && index_ok(word, cx.n_words, cx.status) ? 1u << (j & 31) : 0u;
+}
+
+// The rings of one warp: active words found by the scan, and the active sites they hold.
+constexpr int kWordRingCap = 64;     // uint2 entries: (activity nibbles, lr << 25 | w << 16 | d16)
+constexpr uint32_t kWordRingMask = kWordRingCap - 1;
+constexpr int kSiteRingCap = 512;    // uint32 entries: lr << 18 | j << 2 | direction (< 64 + 256 held)
+constexpr uint32_t kSiteRingMask = kSiteRingCap - 1;
+
+struct Rings {
+    uint2 *words;
+    uint32_t *sites;
+    uint32_t wh, wt, sh, st;  // heads and tails (warp-uniform)
+};
+
+// Warp-uniform: update the next n (<= 64) active sites, two per lane (sites lane and lane + 32).
+// Both decisions are taken before either bit is flipped, so their loads and Philox rounds
+// interleave; sites of one step never read each other's bits, so the order does not matter.
+template <int GAME>
+__device__ __forceinline__ void drain_sites(const Ctx &cx, Rings &q, uint32_t n, int lane) {
+    __syncwarp();
+    const uint32_t l = static_cast<uint32_t>(lane);
+    if (l + 32u < n) {
+        int a0, a1;
+        const uint32_t f0 = site_flip<GAME>(cx, q.sites[(q.sh + l) & kSiteRingMask], a0);
+        const uint32_t f1 = site_flip<GAME>(cx, q.sites[(q.sh + l + 32u) & kSiteRingMask], a1);
+        if (f0) atomicXor(&cx.rows[a0], f0);
+        if (f1) atomicXor(&cx.rows[a1], f1);
+    } else if (l < n) {
+        int a0;
+        const uint32_t f0 = site_flip<GAME>(cx, q.sites[(q.sh + l) & kSiteRingMask], a0);
+        if (f0) atomicXor(&cx.rows[a0], f0);
+    }
+    q.sh += n;
+}
+
+// Warp-uniform: turn the next n (<= 32) active words into site entries, one word per lane (the
+// ring positions from a prefix sum of the lanes' site counts, <= 8, by its bits), then update
+// sites while 64 or more are waiting. The site ring holds < 64 entries before and at most
+// 63 + 256 after.
+template <int OJ, int GAME>
+__device__ __forceinline__ void expand_words(const Ctx &cx, Rings &q, uint32_t n, int lane) {
+    __syncwarp();
+    uint32_t act = 0, y = 0;
+    if (static_cast<uint32_t>(lane) < n) {
+        const uint2 e = q.words[(q.wh + lane) & kWordRingMask];
+        act = e.x;
+        y = e.y;
+    }
+    q.wh += n;
+    const uint32_t c = __popc(act), lt = (1u << lane) - 1u;
+    const uint32_t b0 = __ballot_sync(0xffffffffu, c & 1u), b1 = __ballot_sync(0xffffffffu, c & 2u);
+    const uint32_t b2 = __ballot_sync(0xffffffffu, c & 4u), b3 = __ballot_sync(0xffffffffu, c & 8u);
+    uint32_t pos = q.st + __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt) + 8u * __popc(b3 & lt);
+    q.st += __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2) + 8u * __popc(b3);
+    const uint32_t d16 = y & 0xFFFFu;
+    const uint32_t ebase = (y >> 25) << 18 | (32u * ((y >> 16) & 0x1FFu) + OJ) << 2;
+    while (act) {
+        const int m = (__ffs(act) - 1) >> 2;
+        q.sites[pos & kSiteRingMask] = ebase + (static_cast<uint32_t>(4 * m) << 2) + ((d16 >> (2 * m)) & 3u);
+        ++pos;
+        act &= act - 1u;
+    }
+    while (q.st - q.sh >= 64u) drain_sites<GAME>(cx, q, 64u, lane);
+}
+
+// Activity of the 8 sites of one word (nibble bits): s_x != s_y for the drawn neighbour y. l, c, r:
+// the word and its left and right neighbours in the site's row; uc, ur / dc, dr: the word and
+// its right neighbour in the rows above / below; d16: the sites' direction codes.
+template <int OJ>
+__device__ __forceinline__ uint32_t word_activity(uint32_t l, uint32_t c, uint32_t r, uint32_t uc, uint32_t ur,
+                                                  uint32_t dc, uint32_t dr, uint32_t d16) {
+    uint32_t dd = d16;
+    dd = (dd | (dd << 8)) & 0x00FF00FFu;
+    dd = (dd | (dd << 4)) & 0x0F0F0F0Fu;
+    dd = (dd | (dd << 2)) & 0x33333333u;
+    const uint32_t lo_b = dd & kNib, hi_b = (dd >> 1) & kNib;
+    const uint32_t sx = window<OJ>(l, c, r) & kNib;
+    const uint32_t ye = window<OJ + 1>(l, c, r) & kNib;
+    const uint32_t yw = window<OJ - 1>(l, c, r) & kNib;
+    const uint32_t ys = window<OJ>(0u, dc, dr) & kNib;
+    const uint32_t yn = window<OJ>(0u, uc, ur) & kNib;
+    return sx ^ mux(hi_b, mux(lo_b, ye, yw), mux(lo_b, ys, yn));
+}
+
+// Warp-uniform: append the lanes' active words to the word ring; expand 32 when they are there.
+template <int OJ, int GAME>
+__device__ __forceinline__ void push_word(const Ctx &cx, Rings &q, uint32_t act, int lr, int w, uint32_t d16,
+                                          int lane) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, act != 0u);
+    if (act)
+        q.words[(q.wt + __popc(bal & ((1u << lane) - 1u))) & kWordRingMask] =
+            make_uint2(act, static_cast<uint32_t>(lr) << 25 | static_cast<uint32_t>(w) << 16 | d16);
+    q.wt += __popc(bal);
+    if (q.wt - q.wh >= 32u) expand_words<OJ, GAME>(cx, q, 32u, lane);
+}
+
+// Sublattice rows (local lr = first + 4 k, k < n) of a step.
+struct Range {
+    int first, n;
+};
+
+// The sublattice rows of the current step among local rows [lo, hi) (m4: lr = m4 (mod 4)).
+__device__ __forceinline__ Range srows_in(int m4, int lo, int hi) {
+    Range r{0, 0};
+    if (hi <= lo) return r;
+    r.first = lo + ((m4 - lo) & 3);
+    r.n = r.first < hi ? (hi - r.first + 3) >> 2 : 0;
+    return r;
+}
+
+// Scan the rows of up to three ranges in chunks of 64 words, two consecutive words per lane;
+// chunk K of the ranges' concatenation goes to warp K mod 16, so the warps get equal shares.
+// Before its first chunk in range wait_at or later the warp waits for the halo (`wait` returns
+// false if it never lands), and at the end if it had no such chunk. Active words go to the
+// warp's word ring, and 32 of them at a time to the site ring. The direction draws of a warp's
+// next 4 chunks come from one Philox call per lane (chunk o + lane / 8, call lane mod 8 of the
+// chunk's 8) and reach the lanes that use them by shuffles. Warp-uniform.
+template <int OJ, int GAME, class Wait>
+__device__ __forceinline__ bool scan_step(const Ctx &cx, const Range (&rg)[3], int wait_at, Wait wait, Rings &q,
+                                          int warp, int lane) {
+    const int cpr = cx.cpr;
+    const int n0 = rg[0].n * cpr, n1 = rg[1].n * cpr, total = n0 + n1 + rg[2].n * cpr;
+    bool waited = wait_at < 0;
+    uint4 dcall = make_uint4(0, 0, 0, 0);
+    // row of chunk K and its column chunk
+    auto locate = [&](int K, int &lr, int &c) -> int {
+        int r = 0, kk = K;
+        if (kk >= n0) {
+            kk -= n0;
+            r = 1;
+            if (kk >= n1) {
+                kk -= n1;
+                r = 2;
             }
         }
+        const int qr = static_cast<int>((static_cast<uint32_t>(kk) * cx.cmagic) >> 16);
+        c = kk - qr * cpr;
+        lr = (r == 0 ? rg[0].first : r == 1 ? rg[1].first : rg[2].first) + 4 * qr;  // no indexed array
+        return r;
+    };
+    int o = 0;
+    for (int K = warp; K < total; K += kComputeWarps, ++o) {
+        int lr, c;
+        const int r = locate(K, lr, c);
+        if (!waited && r >= wait_at) {
+            if (!wait()) return false;
+            waited = true;
+        }
+        if ((o & 3) == 0) {
+            const int K2 = K + kComputeWarps * (lane >> 3);
+            uint32_t g = 0, a = 0;
+            if (K2 < total) {
+                int lr2, c2;
+                locate(K2, lr2, c2);
+                int i2 = cx.r0 - cx.H + lr2;
+                if (i2 < 0) i2 += cx.L;
+                else if (i2 >= cx.L) i2 -= cx.L;
+                g = static_cast<uint32_t>(8 * c2 + (lane & 7));
+                a = static_cast<uint32_t>(i2 >> 2);
+            }
+            dcall = make_uint4(g, a, cx.kl, cx.kh_dir);
+#pragma unroll
+            for (int rr = 0; rr < 10; ++rr) philox_round(dcall, cx.rk->k0[rr], cx.rk->k1[rr]);
+        }
+        // words w0 = 64 c + 2 lane and w0 + 1: their 32 direction bits are word lane mod 4 of call
+        // (chunk o, lane / 4), which lane 8 (o mod 4) + lane / 4 holds
+        const int src = 8 * (o & 3) + (lane >> 2);
+        const uint32_t dx = __shfl_sync(0xffffffffu, dcall.x, src), dy = __shfl_sync(0xffffffffu, dcall.y, src);
+        const uint32_t dz = __shfl_sync(0xffffffffu, dcall.z, src), dw = __shfl_sync(0xffffffffu, dcall.w, src);
+        const int comp = lane & 3;
+        const uint32_t d32 = comp == 0 ? dx : comp == 1 ? dy : comp == 2 ? dz : dw;
+        const int w0 = 64 * c + 2 * lane;
+        const bool valid = w0 < cx.Lw;  // Lw is even, so w0 + 1 is valid with w0
+        const int wa = valid ? w0 : 0;
+        const int wp = wa == 0 ? cx.Lw - 1 : wa - 1, wb = wa + 1, wq = wa + 2 == cx.Lw ? 0 : wa + 2;
+        const long long rb = static_cast<long long>(lr - 1) * cx.Lw;
+        const uint32_t *row = cx.rows + (lr - 1) * cx.Lw;
+        auto ld = [&](int rr, int ww) -> uint32_t {
+            return index_ok(rb + rr * cx.Lw + swz(ww), cx.n_words, cx.status) ? row[rr * cx.Lw + swz(ww)] : 0u;
+        };
+        const uint32_t cl = ld(1, wp), ca = ld(1, wa), cb = ld(1, wb), cq = ld(1, wq);
+        const uint32_t ua = ld(0, wa), ub = ld(0, wb), uq = OJ > 0 ? ld(0, wq) : 0u;
+        const uint32_t da = ld(2, wa), db = ld(2, wb), dq = OJ > 0 ? ld(2, wq) : 0u;
+        const uint32_t act0 = valid ? word_activity<OJ>(cl, ca, cb, ua, ub, da, db, d32 & 0xFFFFu) : 0u;
+        const uint32_t act1 = valid ? word_activity<OJ>(ca, cb, cq, ub, uq, db, dq, d32 >> 16) : 0u;
+        push_word<OJ, GAME>(cx, q, act0, lr, wa, d32 & 0xFFFFu, lane);
+        push_word<OJ, GAME>(cx, q, act1, lr, wb, d32 >> 16, lane);
     }
+    // every warp sees the halo load complete before the step ends, even one without a chunk that
+    // reads it: the communication warp reuses the mbarrier, the halo rows and the neighbours'
+    // mailbox slot only after the step's barrier, so the load must have landed by then
+    if (!waited && !wait()) return false;
+    return true;
+}
+
+// All remaining active words and sites of the warp. Warp-uniform.
+template <int OJ, int GAME>
+__device__ __forceinline__ void flush_rings(const Ctx &cx, Rings &q, int lane) {
+    if (q.wt != q.wh) expand_words<OJ, GAME>(cx, q, q.wt - q.wh, lane);
+    while (q.st != q.sh) drain_sites<GAME>(cx, q, min(64u, q.st - q.sh), lane);
+}
+
+// One step: with `split`, first the rows whose reads stay inside the band, then -- once the
+// halo has landed -- the rest; then every remaining active site.
+template <int OJ, int GAME, class Wait>
+__device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
+                                          Rings &q, int warp, int lane) {
+    constexpr int R = kReadRadius<GAME>;
+    Range rg[3] = {{0, 0}, {0, 0}, {0, 0}};
+    int wait_at = -1;
+    // rows [in_lo, in_hi) read band rows only; lo <= H < in_lo and in_hi <= H + nb <= hi
+    const int in_lo = cx.H + R, in_hi = cx.H + nb - R;
+    if (!split) {
+        rg[0] = srows_in(m4, lo, hi);
+    } else if (in_hi <= in_lo) {  // a band too thin for an interior
+        rg[0] = srows_in(m4, lo, hi);
+        wait_at = 0;
+    } else {
+        rg[0] = srows_in(m4, in_lo, in_hi);
+        rg[1] = srows_in(m4, lo, in_lo);
+        rg[2] = srows_in(m4, in_hi, hi);
+        wait_at = 1;
+    }
+    if (!scan_step<OJ, GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
+    flush_rings<OJ, GAME>(cx, q, lane);
+    return true;
 }
 
 // --- TMA bulk copies and the CTA's mbarrier (PTX) ------------------------------------------
@@ -266,23 +505,28 @@ constexpr unsigned int kMbarTries = 1u << 26;
 template <int GAME>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_constant__ ResidentParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
+    constexpr int R = kReadRadius<GAME>;
+    const int L = p.L, Lw = p.Lw, S = p.s, H = p.H;
+    const int b = blockIdx.x, nbnd = p.n_bands;
+    const int r0 = band_start(b, L, nbnd), nb = band_start(b + 1, L, nbnd) - r0;
+    const int nb_max = (L + nbnd - 1) / nbnd;
     uint32_t *s_table = smem;
-    uint32_t *s_rows = smem + kTableEntries;
+    uint32_t *s_rows = smem + kTableEntries;                                   // (nb_max + 2H) rows
+    uint32_t *s_stage = s_rows + static_cast<size_t>(nb_max + 2 * H) * Lw;    // 2H rows when s > 1
+    uint2 *s_wring = reinterpret_cast<uint2 *>(s_stage + (S > 1 ? static_cast<size_t>(2 * H) * Lw : 0));
+    uint32_t *s_sring = reinterpret_cast<uint32_t *>(s_wring + kComputeWarps * kWordRingCap);
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ volatile int s_abort;
-    __shared__ unsigned long long s_warp[kComputeThreads / 32];
-    const int tid = threadIdx.x;
+    __shared__ unsigned long long s_warp[kComputeWarps];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool comm = tid >= kComputeThreads;  // the last warp exchanges halos, the others compute
-    const int b = blockIdx.x, nbnd = p.n_bands;
-    const int L = p.L, Lw = p.Lw;
-    const int r0 = band_start(b, L, nbnd), nb = band_start(b + 1, L, nbnd) - r0;
     const int up = (b + nbnd - 1) % nbnd, down = (b + 1) % nbnd;
-    const size_t edge = static_cast<size_t>(3) * Lw;                  // words of 3 rows
+    const size_t edge = static_cast<size_t>(H) * Lw;                  // words of H rows
     const uint32_t edge_bytes = static_cast<uint32_t>(edge * sizeof(uint32_t));
-    const PhiloxKeys rk = p.rk;
+    const PhiloxKeys &rk = p.rk;  // read from the parameter space: constant operands
     // bulk copies need 16-byte aligned rows (the same answer in every CTA: all stop together)
-    if ((smem_u32(s_rows) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u ||
-        (reinterpret_cast<uintptr_t>(p.lat8) & 15u) != 0u) {
+    if ((smem_u32(s_rows) & 15u) != 0u || (smem_u32(s_stage) & 15u) != 0u ||
+        (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.lat8) & 15u) != 0u) {
         if (tid == 0) atomicOr(p.status, 2);
         return;
     }
@@ -291,18 +535,19 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         s_abort = 0;
         mbar_init(&s_mbar, 1);
     }
-    // stage the table and band + halo (rows r0 - 3 .. r0 + nb + 2, periodic) with 4-byte
-    // asynchronous copies (cp.async: many loads in flight per thread, each word to its place);
-    // thread t copies column t mod Lw of every (T / Lw)-th row, so a copy costs a few adds
+    // stage band + halo (rows r0 - H .. r0 + nb + H - 1, periodic) with 4-byte asynchronous
+    // copies (cp.async: many loads in flight per thread, each word to its place); thread t
+    // copies column t mod Lw of every (T / Lw)-th row, so a copy costs a few adds
+    const int n_local = nb + 2 * H;
     const int rows_per_pass = kResThreads / Lw;   // >= 1: a resident row has at most 448 words
     const int col = tid % Lw, row_first = tid / Lw;
     const int scol = swz(col);
     if (row_first < rows_per_pass) {
-        int g = wrap_small(r0 - 3 + row_first, L);
+        int g = wrap_small(r0 - H + row_first, L);
         if (p.lat8) {
             // uint8 lattice: the word's 32 bytes in two 16-byte loads (rows start 256-byte aligned)
 #pragma unroll 4
-            for (int lr = row_first; lr < nb + 6; lr += rows_per_pass) {
+            for (int lr = row_first; lr < n_local; lr += rows_per_pass) {
                 const size_t off = static_cast<size_t>(g) * L + 32 * static_cast<size_t>(col);
                 if (index_ok(static_cast<long long>(off) + 31, static_cast<long long>(L) * L, p.status)) {
                     const uint4 *src = reinterpret_cast<const uint4 *>(p.lat8 + off);
@@ -312,7 +557,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 if (g >= L) g -= L;
             }
         } else {
-            for (int lr = row_first; lr < nb + 6; lr += rows_per_pass) {
+            for (int lr = row_first; lr < n_local; lr += rows_per_pass) {
                 if (index_ok(static_cast<long long>(g) * Lw + col, static_cast<long long>(L) * Lw, p.status))
                     copy_async4(&s_rows[lr * Lw + scol], &p.lat[static_cast<size_t>(g) * Lw + col]);
                 g += rows_per_pass;
@@ -323,115 +568,152 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     copy_async_wait_all();
     fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
     __syncthreads();
+
+    Ctx cx;
+    cx.rows = s_rows;
+    cx.table = s_table;
+    cx.L = L;
+    cx.Lw = Lw;
+    cx.r0 = r0;
+    cx.H = H;
+    cx.rk = &rk;
+    cx.cpr = (Lw + 63) >> 6;
+    cx.cmagic = (65536u + static_cast<uint32_t>(cx.cpr) - 1u) / static_cast<uint32_t>(cx.cpr);
+    cx.n_words = static_cast<long long>(n_local) * Lw;
+    cx.status = p.status;
+    Rings q;
+    q.words = s_wring + (warp < kComputeWarps ? warp : 0) * kWordRingCap;
+    q.sites = s_sring + (warp < kComputeWarps ? warp : 0) * kSiteRingCap;
+    q.wh = q.wt = q.sh = q.st = 0;
     uint4 ocall = make_uint4(0, 0, 0, 0);
     uint64_t ocall_idx = ~0ull;
-    const int total = 16 * p.n_mcs;
+    const int n_blocks = 16 * p.n_mcs / S;
     bool load_pending = false;  // communication lane: a halo load not yet seen complete
-    for (int j = 0; j < total; ++j) {
-        const uint64_t k = p.k0 + static_cast<uint64_t>(j);
-        if (comm) {
-            // fetch the neighbours' rows after step j - 1 into the halo, asynchronously
-            if (tid == kComputeThreads && j > 0) {
-                unsigned int it = 0;
-                const unsigned int want = p.ctr_base + static_cast<unsigned int>(j);
-                while ((load_acquire(&p.ctr[up]) < want || load_acquire(&p.ctr[down]) < want) && it < p.spin_limit) {
-                    __nanosleep(32);
-                    ++it;
-                }
-                if (it >= p.spin_limit) {
-                    atomicOr(p.status, 1);
-                    s_abort = 1;
-                } else {
-                    const int par = (j - 1) & 1;
-                    const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * edge;
-                    const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * edge;
-                    fence_async_global();  // the acquired rows, for the async proxy's reads
-                    mbar_expect_tx(&s_mbar, 2 * edge_bytes);
-                    bulk_load(s_rows, from_up, edge_bytes, &s_mbar);
-                    bulk_load(s_rows + static_cast<size_t>(nb + 3) * Lw, from_down, edge_bytes, &s_mbar);
-                    load_pending = true;
-                }
-            }
-            __syncwarp();
-        } else {
-            if ((k >> 5) != ocall_idx) {
-                ocall_idx = k >> 5;
-                ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
-                                             kTagOffset), rk);
-            }
-            const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
-            const BandRows br = band_rows<GAME>(r0, nb, o >> 2);
-            // interior rows read only the band's own rows: they run while the halo is in flight
-            switch (o & 3) {
-                case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
-                case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
-                case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
-                default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, false, k, p.status); break;
-            }
-            bool ready = true;
-            if (j > 0) {
-                unsigned int it = 0;
-                while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>((j - 1) & 1))) {
-                    if (s_abort || ++it >= kMbarTries) {
-                        ready = false;
-                        break;
+    for (int blk = 0; blk < n_blocks; ++blk) {
+        for (int jb = 0; jb < S; ++jb) {
+            const int j = blk * S + jb;
+            const uint64_t k = p.k0 + static_cast<uint64_t>(j);
+            const bool fresh_halo = jb == 0 && blk > 0;  // the halo is being refreshed for this step
+            if (comm) {
+                // fetch the neighbours' rows after block blk - 1 into the halo, asynchronously
+                if (tid == kComputeThreads && fresh_halo) {
+                    unsigned int it = 0;
+                    const unsigned int want = p.ctr_base + static_cast<unsigned int>(blk);
+                    while ((load_acquire(&p.ctr[up]) < want || load_acquire(&p.ctr[down]) < want) && it < p.spin_limit) {
+                        __nanosleep(32);
+                        ++it;
+                    }
+                    if (it >= p.spin_limit) {
+                        atomicOr(p.status, 1);
+                        s_abort = 1;
+                    } else {
+                        const int par = (blk - 1) & 1;
+                        const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * edge;
+                        const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * edge;
+                        fence_async_global();  // the acquired rows, for the async proxy's reads
+                        mbar_expect_tx(&s_mbar, 2 * edge_bytes);
+                        bulk_load(s_rows, from_up, edge_bytes, &s_mbar);
+                        bulk_load(s_rows + static_cast<size_t>(nb + H) * Lw, from_down, edge_bytes, &s_mbar);
+                        load_pending = true;
                     }
                 }
-            }
-            if (ready) {
-                // the at most two edge rows, which read the halo
-                switch (o & 3) {
-                    case 0: resident_step<0, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
-                    case 1: resident_step<1, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
-                    case 2: resident_step<2, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
-                    default: resident_step<3, GAME>(s_rows, s_table, rk, Lw, r0, nb, br, true, k, p.status); break;
-                }
+                __syncwarp();
             } else {
-                s_abort = 1;
-            }
-            fence_async_shared();  // this thread's lattice writes, for the bulk store below
-        }
-        __syncthreads();
-        if (s_abort) {
-            // a wait ran out: make sure no bulk copy still targets this CTA's shared memory,
-            // then stop; the lattice in global memory is left as it was
-            if (tid == kComputeThreads && load_pending) {
-                unsigned int it = 0;
-                while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>((j - 1) & 1)) && ++it < kMbarTries) {
+                if ((k >> 5) != ocall_idx) {
+                    ocall_idx = k >> 5;
+                    ocall = philox_rk(make_uint4(static_cast<uint32_t>(ocall_idx), static_cast<uint32_t>(ocall_idx >> 32), 0u,
+                                                 kTagOffset), rk);
                 }
-                // the halo load was never seen to land: the CTA leaves with a copy into its
-                // shared memory possibly in flight, which the host must treat as fatal
-                if (it >= kMbarTries) atomicOr(p.status, 8);
+                const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
+                cx.kl = static_cast<uint32_t>(k);
+                cx.kh_dir = static_cast<uint32_t>(k >> 32) | kTagDir;
+                cx.kh_u = static_cast<uint32_t>(k >> 32) | kTagU;
+                // local row lr is global row r0 - H + lr: a sublattice row iff lr = oi - r0 + H (mod 4)
+                const int m4 = ((o >> 2) - r0 + H) & 3;
+                const int e = R * (S - 1 - jb);  // halo rows updated on each side in this step
+                const int lo = H - e, hi = H + nb + e;
+                const int parity = (blk - 1) & 1;
+                auto wait = [&]() -> bool {
+                    unsigned int it = 0;
+                    while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>(parity))) {
+                        if (s_abort || ++it >= kMbarTries) return false;
+                    }
+                    return true;
+                };
+                bool ok = true;
+                switch (o & 3) {
+                    case 0: ok = step_rows<0, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
+                    case 1: ok = step_rows<1, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
+                    case 2: ok = step_rows<2, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
+                    default: ok = step_rows<3, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
+                }
+                if (!ok) {
+                    s_abort = 1;
+                    q.wh = q.wt;  // the step is abandoned
+                    q.sh = q.st;
+                }
+                __syncwarp();
+                fence_async_shared();  // this thread's lattice writes, for the bulk store below
             }
-            return;
-        }
-        load_pending = false;
-        if (comm) {
-            // publish the band's top and bottom 3 rows (as laid out in shared memory) for the
-            // neighbours' next step; the compute warps meanwhile start step j + 1, which
-            // writes neither
-            if (tid == kComputeThreads) {
-                uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 0) * edge;
-                uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (j & 1)) * 2 + 1) * edge;
-                bulk_store(to_top, s_rows + static_cast<size_t>(3) * Lw, edge_bytes);
-                bulk_store(to_bot, s_rows + static_cast<size_t>(nb) * Lw, edge_bytes);
-                bulk_commit_and_wait();
-                fence_async_global();
-                __threadfence();
-                store_release(&p.ctr[b], p.ctr_base + static_cast<unsigned int>(j + 1));
+            __syncthreads();
+            if (s_abort) {
+                // a wait ran out: make sure no bulk copy still targets this CTA's shared memory,
+                // then stop; the lattice in global memory is left as it was
+                if (tid == kComputeThreads && load_pending) {
+                    unsigned int it = 0;
+                    while (!mbar_try_wait(&s_mbar, static_cast<uint32_t>((blk - 1) & 1)) && ++it < kMbarTries) {
+                    }
+                    // the halo load was never seen to land: the CTA leaves with a copy into its
+                    // shared memory possibly in flight, which the host must treat as fatal
+                    if (it >= kMbarTries) atomicOr(p.status, 8);
+                }
+                return;
             }
-            __syncwarp();
-        } else if ((j & 15) == 15 && p.counts) {
-            unsigned long long c = 0;
-            for (int x = tid; x < nb * Lw; x += kComputeThreads) c += __popc(s_rows[3 * Lw + x]);
+            if (fresh_halo) load_pending = false;
+            if (jb == S - 1) {
+                // publish the band's top and bottom H rows for the neighbours' next block. With
+                // s > 1 the next block's first step may update some of them before the copy has
+                // read them, so they are snapshotted into the staging rows first.
+                const uint32_t *top = s_rows + static_cast<size_t>(H) * Lw;
+                const uint32_t *bot = s_rows + static_cast<size_t>(nb) * Lw;
+                if (S > 1) {
+                    if (!comm) {
+                        for (int x = tid; x < static_cast<int>(edge); x += kComputeThreads) {
+                            s_stage[x] = top[x];
+                            s_stage[edge + x] = bot[x];
+                        }
+                        fence_async_shared();
+                    }
+                    __syncthreads();
+                    top = s_stage;
+                    bot = s_stage + edge;
+                }
+                if (comm) {
+                    if (tid == kComputeThreads) {
+                        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 0) * edge;
+                        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 1) * edge;
+                        bulk_store(to_top, top, edge_bytes);
+                        bulk_store(to_bot, bot, edge_bytes);
+                        bulk_commit_and_wait();
+                        fence_async_global();
+                        __threadfence();
+                        store_release(&p.ctr[b], p.ctr_base + static_cast<unsigned int>(blk + 1));
+                    }
+                    __syncwarp();
+                }
+            }
+            if (!comm && (j & 15) == 15 && p.counts) {
+                unsigned long long c = 0;
+                for (int x = tid; x < nb * Lw; x += kComputeThreads) c += __popc(s_rows[H * Lw + x]);
 #pragma unroll
-            for (int s = 16; s > 0; s >>= 1) c += __shfl_down_sync(0xffffffffu, c, s);
-            if ((tid & 31) == 0) s_warp[tid >> 5] = c;
-            compute_barrier();
-            if (tid == 0) {
-                unsigned long long tot = 0;
-                for (int w = 0; w < kComputeThreads / 32; ++w) tot += s_warp[w];
-                atomicAdd(&p.counts[j >> 4], tot);
+                for (int sft = 16; sft > 0; sft >>= 1) c += __shfl_down_sync(0xffffffffu, c, sft);
+                if (lane == 0) s_warp[warp] = c;
+                compute_barrier();
+                if (tid == 0) {
+                    unsigned long long tot = 0;
+                    for (int w = 0; w < kComputeWarps; ++w) tot += s_warp[w];
+                    atomicAdd(&p.counts[j >> 4], tot);
+                }
             }
         }
     }
@@ -442,7 +724,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
             for (int lr = row_first; lr < nb; lr += rows_per_pass) {
                 const size_t off = static_cast<size_t>(r0 + lr) * L + 32 * static_cast<size_t>(col);
                 if (index_ok(static_cast<long long>(off) + 31, static_cast<long long>(L) * L, p.status)) {
-                    const uint32_t w = s_rows[(lr + 3) * Lw + scol];
+                    const uint32_t w = s_rows[(lr + H) * Lw + scol];
                     uint4 *dst = reinterpret_cast<uint4 *>(p.lat8 + off);
                     dst[0] = unpack_bits16(w & 0xFFFFu);
                     dst[1] = unpack_bits16(w >> 16);
@@ -451,37 +733,63 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         } else {
             for (int lr = row_first; lr < nb; lr += rows_per_pass) {
                 if (index_ok(static_cast<long long>(r0 + lr) * Lw + col, static_cast<long long>(L) * Lw, p.status))
-                    p.lat[static_cast<size_t>(r0 + lr) * Lw + col] = s_rows[(lr + 3) * Lw + scol];
+                    p.lat[static_cast<size_t>(r0 + lr) * Lw + col] = s_rows[(lr + H) * Lw + scol];
             }
         }
     }
 }
 
+// Shared memory of a launch: table, band + halo rows, staging rows (s > 1), the warps' rings.
+size_t resident_smem_bytes(int L, int n_bands, int game, int s) {
+    const int H = kReadRadius<kGroupGame> * s;  // the group game's halo bounds the pairwise game's
+    (void)game;
+    const size_t Lw = static_cast<size_t>(L / 32);
+    const size_t max_rows = static_cast<size_t>((L + n_bands - 1) / n_bands);
+    return sizeof(uint32_t) * (kTableEntries + (max_rows + 2 * H) * Lw + (s > 1 ? 2 * H * Lw : 0)) +
+           static_cast<size_t>(kComputeWarps) * (kWordRingCap * sizeof(uint2) + kSiteRingCap * sizeof(uint32_t));
+}
+
 }  // namespace
 
-// Bands for a lattice of side L: one per SM when every band keeps at least 4 rows and its
-// rows fit the shared memory; 0 when the lattice cannot be resident. The kernel works on the
-// bit-packed form; a uint8 lattice is packed for the call by the caller.
+// Bands for a lattice of side L: one per SM when every band keeps at least 3 rows (the rows a
+// block of one step publishes must be band rows) and its rows fit the shared memory with one
+// step per exchange; 0 when the lattice cannot be resident.
 int resident_bands(int layout, int L, int sms, size_t smem_optin) {
     (void)layout;
     if (L < 256 || L % 256 != 0 || sms < 1) return 0;
     int n = sms;
-    while (n > 1 && L / n < 4) --n;
+    while (n > 1 && L / n < kReadRadius<kGroupGame>) --n;
     const int max_rows = (L + n - 1) / n;
-    const size_t need = sizeof(uint32_t) * (kTableEntries + static_cast<size_t>(max_rows + 6) * (L / 32));
-    return need <= smem_optin ? n : 0;
+    return resident_smem_bytes(L, n, kGroupGame, 1) <= smem_optin && max_rows + 6 <= kMaxLocalRows && L / 32 <= kMaxRowWords
+               ? n
+               : 0;
 }
 
-size_t resident_mailbox_words(int L, int n_bands) { return static_cast<size_t>(n_bands) * 2 * 2 * 3 * (L / 32); }
+// Largest s in {4, 2, 1} (sublattice steps per halo exchange) whose rows fit the shared memory.
+int resident_max_steps_per_exchange(int L, int n_bands, size_t smem_optin) {
+    const int max_rows = (L + n_bands - 1) / n_bands;
+    for (int s = kMaxStepsPerExchange; s > 1; s >>= 1)
+        if (resident_smem_bytes(L, n_bands, kGroupGame, s) <= smem_optin && L / n_bands >= 3 * s &&
+            max_rows + 6 * s <= kMaxLocalRows)
+            return s;
+    return 1;
+}
+
+size_t resident_mailbox_words(int L, int n_bands) { return static_cast<size_t>(n_bands) * 2 * 2 * kMaxHalo * (L / 32); }
 
 cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     if (a.n_bands < 1 || a.L % 256 != 0) return cudaErrorInvalidValue;
+    if (a.steps_per_exchange != 1 && a.steps_per_exchange != 2 && a.steps_per_exchange != 4) return cudaErrorInvalidValue;
     ResidentParams p;
     p.lat = a.lat;
     p.lat8 = a.lat8;
     p.L = a.L;
     p.Lw = a.L / 32;
     p.n_bands = a.n_bands;
+    p.s = a.steps_per_exchange;
+    p.H = (a.game == kPairGame ? kReadRadius<kPairGame> : kReadRadius<kGroupGame>) * p.s;
+    if (a.L / a.n_bands < p.H) return cudaErrorInvalidValue;  // published rows must be band rows
+    if ((a.L + a.n_bands - 1) / a.n_bands + 2 * p.H > kMaxLocalRows || p.Lw > kMaxRowWords) return cudaErrorInvalidValue;
     p.seed = a.seed;
     p.k0 = a.k0;
     p.n_mcs = a.n_mcs;
@@ -493,8 +801,7 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.status = a.status;
     p.spin_limit = a.spin_limit;
     p.rk = philox_round_keys(a.seed);
-    const int max_rows = (a.L + a.n_bands - 1) / a.n_bands;
-    const size_t smem = sizeof(uint32_t) * (kTableEntries + static_cast<size_t>(max_rows + 6) * p.Lw);
+    const size_t smem = resident_smem_bytes(a.L, a.n_bands, a.game, p.s);
     const void *kernel = a.game == kPairGame ? reinterpret_cast<const void *>(k_resident<kPairGame>)
                                              : reinterpret_cast<const void *>(k_resident<kGroupGame>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

@@ -4,10 +4,12 @@ The batched-replica workload: n replicas with L drawn uniformly from {64, 128, 2
 1024}, r uniform in [3.5, 4.2], K = 0.5, independent seeds, Bernoulli(1/2) starts (Section
 III), n_mcs MCS each; the batch autotuner picks the CTA size and warps per replica, the
 persistent launch is captured in a CUDA graph. For comparison the same replicas are also
-advanced with one launch sequence per replica through the single-lattice path (timed on a
-subset, scaled per replica-MCS).
+advanced with one launch sequence per replica through the single-lattice path: all of them for
+the same number of MCS (--compare-all, measured), or a sample whose rate is scaled to the
+workload.
 
     python -m paper_1704_08098_gb300.replicas --n 512 --mcs 5000
+    python -m paper_1704_08098_gb300.replicas --n 512 --mcs 200 --compare-all
 """
 from __future__ import annotations
 
@@ -63,26 +65,39 @@ def run(n: int = 512, n_mcs: int = 5000, chunk: int = 500, tune_mcs: int = 20,
                         "absorbed": int((counts[:, -1] == 0).sum())}
     if not compare:
         return out
-    # one launch sequence per replica (the single-lattice API), on a sample of replicas
-    idx = np.random.default_rng(seed).choice(n, size=min(per_replica_sample, n), replace=False)
+    # one launch sequence per replica (the single-lattice API): every replica when
+    # per_replica_sample >= n (a measured comparison over the same MCS), else a sample of them
+    # whose rate is scaled to the workload
+    full = per_replica_sample >= n
+    idx = np.arange(n) if full else np.random.default_rng(seed).choice(n, size=per_replica_sample, replace=False)
+    mcs = n_mcs if full else per_replica_mcs
     per_ms = 0.0
     sample_sites = 0.0
+    per_counts_match = True
     for i in idx:
         with pgg.Lattice(int(L[i]), float(r[i]), 0.5, layout="bitpack", stream=stream.cuda_stream) as lat:
             lat.seed(int(seeds[i]), 0.5)
-            lat.advance(2)
+            if not full:
+                lat.advance(2)
             torch.cuda.synchronize()
             e0.record(stream)
-            lat.advance(per_replica_mcs)
+            lat.advance(mcs)
             e1.record(stream)
             torch.cuda.synchronize()
             per_ms += e0.elapsed_time(e1)
-            sample_sites += float(L[i]) ** 2 * per_replica_mcs
+            sample_sites += float(L[i]) ** 2 * mcs
+            if full:
+                per_counts_match &= lat.count() == int(counts[i, -1])
     rate = sample_sites / (per_ms / 1e3)
-    out["per_replica"] = {"site_updates_per_s": rate, "sample_replicas": int(len(idx)),
-                          "sample_mcs": per_replica_mcs,
-                          "est_gpu_s_for_workload": sites_per_mcs * n_mcs / rate}
-    out["speedup"] = out["per_replica"]["est_gpu_s_for_workload"] / out["batched"]["gpu_s"]
+    if full:
+        out["per_replica"] = {"gpu_s": per_ms / 1e3, "site_updates_per_s": rate, "replicas": int(n), "mcs": mcs,
+                              "measured": True, "final_counts_equal_batched": bool(per_counts_match)}
+        out["speedup"] = out["per_replica"]["gpu_s"] / out["batched"]["gpu_s"]
+    else:
+        out["per_replica"] = {"site_updates_per_s": rate, "sample_replicas": int(len(idx)),
+                              "sample_mcs": per_replica_mcs, "measured": False,
+                              "est_gpu_s_for_workload": sites_per_mcs * n_mcs / rate}
+        out["speedup"] = out["per_replica"]["est_gpu_s_for_workload"] / out["batched"]["gpu_s"]
     return out
 
 
@@ -93,9 +108,13 @@ def main():
     ap.add_argument("--chunk", type=int, default=500)
     ap.add_argument("--no-autotune", action="store_true", help="library default CTA size and team warps")
     ap.add_argument("--no-compare", action="store_true", help="skip the one-launch-sequence-per-replica timing")
+    ap.add_argument("--compare-all", action="store_true",
+                    help="run every replica through the single-lattice path for the same MCS (measured, "
+                         "not extrapolated from a sample)")
     args = ap.parse_args()
     print(json.dumps(run(args.n, args.mcs, args.chunk, autotune=not args.no_autotune,
-                         compare=not args.no_compare)))
+                         compare=not args.no_compare,
+                         per_replica_sample=args.n if args.compare_all else 16)))
 
 
 if __name__ == "__main__":

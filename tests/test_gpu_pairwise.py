@@ -136,6 +136,19 @@ def test_pair_resident_kernel(o, pgg, L, n_mcs, layout):
     assert np.array_equal(got_lat, want_lat)
 
 
+@pytest.mark.parametrize("layout", ["bitpack", "u8"])
+@pytest.mark.parametrize("L,spe,n_mcs", [(1024, 1, 5), (2048, 2, 3), (2048, 4, 3)])
+def test_pair_resident_steps_per_exchange(o, pgg, L, spe, n_mcs, layout):
+    """The pairwise game on the resident kernel with 1, 2 or 4 steps per halo exchange (halo of
+    2 rows per step: the game reads one line less, Section VI)."""
+    want_lat, want_counts = run_oracle(o, L, SNOWDRIFT, 0.5, 95 + L + spe, n_mcs)
+    got_lat, got_counts, k = run_gpu(pgg, L, SNOWDRIFT, 0.5, 95 + L + spe, n_mcs, layout,
+                                     dict(kernel="resident", tile_y=spe))
+    assert k == 16 * n_mcs
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
 @pytest.mark.parametrize("layout", ["u8", "bitpack"])
 def test_pair_full_size_default_schedule(o, pgg, layout):
     """L = 8192 (bit-packed) / 4096 (uint8) in the default (tuned) launch configuration."""

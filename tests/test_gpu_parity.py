@@ -419,6 +419,39 @@ def test_resident_kernel(o, pgg, L, n_mcs, layout):
     assert np.array_equal(got_lat, want_lat)
 
 
+@pytest.mark.parametrize("layout", ["bitpack", "u8"])
+@pytest.mark.parametrize("L,spe,n_mcs", [(1024, 1, 6), (1024, 2, 6), (2048, 4, 3), (2816, 2, 2), (4096, 4, 2),
+                                         (4096, 1, 2)])
+def test_resident_steps_per_exchange(o, pgg, L, spe, n_mcs, layout):
+    """The resident kernel with its halo exchanged every 1, 2 or 4 sublattice steps (the halo
+    rows updated redundantly in between) against the oracle; L = 2816 has bands of 18 and 19
+    rows."""
+    want_lat, want_counts = run_oracle(o, L, 3.8, 0.5, 70 + L + spe, n_mcs)
+    got_lat, got_counts, k = run_gpu(pgg, L, 3.8, 0.5, 70 + L + spe, n_mcs, layout,
+                                     dict(kernel="resident", tile_y=spe))
+    assert k == 16 * n_mcs
+    assert np.array_equal(got_counts, want_counts)
+    assert np.array_equal(got_lat, want_lat)
+
+
+def test_resident_steps_per_exchange_limits(pgg):
+    """Steps per exchange: 1, 2 or 4, and only as many as the bands' rows and the shared memory
+    allow (bands of 6-7 rows at L = 1024 take at most 2); the default is the largest that fits."""
+    with pgg.Lattice(1024, 3.8, 0.5, layout="bitpack") as lat:
+        for bad in (3, 5, -1):
+            with pytest.raises(pgg.PGGError):
+                lat.set_schedule("resident", 16, 0, bad)
+        with pytest.raises(pgg.PGGError):
+            lat.set_schedule("resident", 16, 0, 4)
+        lat.set_schedule("resident")
+        assert lat.schedule()["tile_y"] == 2
+    with pgg.Lattice(8192, 3.8, 0.5, layout="bitpack") as lat:
+        lat.set_schedule("resident")
+        assert lat.schedule()["tile_y"] == 4
+        lat.set_schedule("resident", 16, 0, 1)
+        assert lat.schedule()["tile_y"] == 1
+
+
 def test_resident_full_size_and_resume(o, pgg):
     L = 8192
     want_lat, want_counts = run_oracle(o, L, 3.744, 0.5, 1, 2)
