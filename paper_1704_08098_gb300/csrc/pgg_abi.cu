@@ -551,9 +551,12 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     if (s.kernel == PGG_KERNEL_RESIDENT) {
         const int bands = s.tile_x;
         if (bands < 1) return fail(PGG_ERR_STATE, "pgg_step_mcs: the lattice cannot be resident");
+        const size_t mb_words = pgg::resident_mailbox_words(c->L, bands);
         if (!c->mailbox_d) {
-            cudaError_t e = cudaMalloc(&c->mailbox_d, pgg::resident_mailbox_words(c->L, bands) * sizeof(uint32_t));
+            // the mailbox, then one word per band that the kernel keeps between launches
+            cudaError_t e = cudaMalloc(&c->mailbox_d, (mb_words + bands) * sizeof(uint32_t));
             if (e == cudaSuccess) e = cudaMalloc(&c->ctr_d, sizeof(unsigned int) * bands);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->mailbox_d + mb_words, 0, sizeof(uint32_t) * bands, c->stream);
             if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(resident buffers): %s", cudaGetErrorString(e));
         }
         // the kernel keeps the band bit-packed in shared memory; a uint8 lattice is packed as it is
@@ -572,6 +575,11 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         a.status = c->status_d;
         a.spin_limit = c->spin_limit;
         a.steps_per_exchange = s.tile_y;
+        a.hint = reinterpret_cast<unsigned int *>(c->mailbox_d + mb_words);
+        // the pass over active sites only wins for the group game up to about 10 % of a step's
+        // sites adopting (measured at L = 8192); the pairwise game, whose active sites are more
+        // numerous and cheaper to update whole words at a time, takes the dense pass above 1.5 %
+        a.dense_per_mille = c->game == PGG_GAME_PAIRWISE ? 15u : 100u;
         // one launch covers at most 1 << 16 MCS
         for (int64_t m0 = 0; m0 < n_mcs; m0 += (1 << 16)) {
             a.n_mcs = static_cast<int>(std::min<int64_t>(n_mcs - m0, 1 << 16));

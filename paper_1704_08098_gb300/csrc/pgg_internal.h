@@ -93,6 +93,9 @@ struct ResidentArgs {
                                   // possibly in flight (fatal for the device context)
     unsigned int spin_limit;      // polls before a wait gives up
     int steps_per_exchange = 1;   // sublattice steps between halo exchanges: 1, 2 or 4
+    unsigned int *hint = nullptr; // n_bands words kept between launches (pass-choice hint), nullable
+    unsigned int dense_per_mille = 100;  // a step takes the dense pass when the previous one flipped
+                                         // more than this share (per mille) of its sites
 };
 int resident_bands(int layout, int L, int sms, size_t smem_optin);
 // Largest steps_per_exchange (4, 2 or 1) whose halo rows fit the shared memory.

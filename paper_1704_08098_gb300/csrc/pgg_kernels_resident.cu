@@ -29,12 +29,15 @@
 // draw (the stream is counter based). Each warp therefore scans words of its sublattice rows
 // (8 sites per 32-column word, the direction draws of 8 words from one Philox call), finds the
 // active sites (s_x != s_y for the drawn neighbour y), and appends them to a ring in shared
-// memory; whenever the ring holds 32 entries, the warp updates them, one site per lane: the
-// group counts S_x and S_y from the 7 x 7 neighbourhood of x (population counts of masked
-// bits), the threshold of Eq. (3) from the host-built table, the adoption draw, and an atomic
-// XOR of the site's bit when it adopts. So the costly part runs at full warp width on active
-// sites only. Updates of one step touch disjoint sites and read only bits no other update of
-// the step changes, so they run in place in any order.
+// memory (active words first, then their sites); whenever 64 sites are waiting, the warp updates
+// them, two per lane: the group counts S_x and S_y from the 7 x 7 neighbourhood of x (population
+// counts of masked bits), the threshold of Eq. (3) from the host-built table, the adoption draw,
+// and an atomic XOR of the site's bit when it adopts. So the costly part runs at full warp width
+// on active sites only. When many sites are active (a random start, the pairwise game), a dense
+// pass does better: every word, all 8 sites at once, by the shared per-word core of
+// pgg_unit.cuh. Each step takes one pass or the other, chosen from the number of adoptions in
+// the CTA's previous step; both give the same result. Updates of one step touch disjoint sites
+// and read only bits no other update of the step changes, so they run in place in any order.
 //
 // The count after each MCS is the sum of the bands' population counts. The band is staged
 // with 4-byte cp.async copies and written back once per launch; a uint8 lattice is packed as
@@ -44,6 +47,7 @@
 
 #include "pgg_device.cuh"
 #include "pgg_internal.h"
+#include "pgg_unit.cuh"
 
 namespace pgg {
 namespace {
@@ -55,8 +59,6 @@ constexpr int kMaxStepsPerExchange = 4;
 constexpr int kMaxHalo = 3 * kMaxStepsPerExchange;    // halo rows per side at most
 constexpr int kMaxLocalRows = 128;                     // band + halo rows (7 bits of a word entry)
 constexpr int kMaxRowWords = 512;                      // words per row (9 bits of a word entry)
-
-constexpr uint32_t kNib = 0x11111111u;
 
 struct ResidentParams {
     uint32_t *lat;            // bit-packed global lattice (read at the start, written at the end)
@@ -73,6 +75,8 @@ struct ResidentParams {
     int *status;              // | 1 a wait timed out, | 2 misaligned buffers, | 4 an index check failed (checked build),
                               // | 8 a CTA stopped with a halo load possibly still in flight
     unsigned int spin_limit;
+    unsigned int *hint;       // [band] adoptions of the last step of the previous launch (nullable)
+    unsigned int dense_per_mille;  // dense pass above this share (per mille) of a step's sites flipped
     PhiloxKeys rk;
 };
 
@@ -95,13 +99,6 @@ __device__ __forceinline__ uint4 unpack_bits16(uint32_t h) {
                       unpack_bits4((h >> 12) & 15u));
 }
 
-// Periodic wrap of an index that may be a few periods outside [0, m).
-__device__ __forceinline__ int wrap_small(int v, int m) {
-    while (v < 0) v += m;
-    while (v >= m) v -= m;
-    return v;
-}
-
 __device__ __forceinline__ int band_start(int b, int L, int n) { return static_cast<int>((static_cast<long long>(b) * L) / n); }
 
 // Word w of a band row lives at (w ^ ((w >> 5) & 7)): lanes that read words 1, 2, 4 or 8 apart
@@ -118,32 +115,21 @@ __device__ __forceinline__ void store_release(unsigned int *p, unsigned int v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// The 32 columns starting D columns to the right (D < 0: left) of the word whose left, centre
-// and right neighbours are l, c, r.
-template <int D>
-__device__ __forceinline__ uint32_t window(uint32_t l, uint32_t c, uint32_t r) {
-    static_assert(D >= -4 && D <= 4, "window shift out of range");
-    if constexpr (D == 0) return c;
-    else if constexpr (D > 0) return __funnelshift_r(c, r, D);
-    else return __funnelshift_l(l, c, -D);
-}
-
-__device__ __forceinline__ uint32_t mux(uint32_t sel, uint32_t if0, uint32_t if1) { return (if0 & ~sel) | (if1 & sel); }
-
-// --- the 7 x 7 neighbourhood of a site as 49 bits -------------------------------------------
-// Bit 7 r + t holds the site at (row offset r - 3, column offset t - 3); the site itself is bit
-// 24. Relative to a centre at bit 24, the group count sum of Section III, S = sum of the 5
-// group counts of the groups the centre belongs to (Fig. 1), weighs the centre 5 times, its 4
-// nearest neighbours and 4 diagonal neighbours twice, and the 4 sites two steps away along the
-// axes once (a neighbour w of z lies in z's own group and in w's; a diagonal site in the groups
-// of the two neighbours it shares with z; an axis site at distance 2 in the group of the
-// neighbour between them).
-constexpr uint32_t kOnesLo = (1u << 10) | (1u << 22) | (1u << 26);   // (-2, 0), (0, -2), (0, +2)
-constexpr uint32_t kOnesHi = 1u << (38 - 32);                         // (+2, 0)
-constexpr uint32_t kTwosLo = (1u << 16) | (1u << 17) | (1u << 18) | (1u << 23) | (1u << 25) | (1u << 30) | (1u << 31);
-constexpr uint32_t kTwosHi = 1u << (32 - 32);                         // (+1, +1)
+// --- the 7 x 7 neighbourhood of a site, one byte per row ------------------------------------
+// Byte r holds row offset r - 3 and bit t of it column offset t - 3 (t = 7, column offset +4, is
+// carried along and never used); the site itself is bit 27. Relative to a centre at bit 27, the
+// group count sum of Section III, S = sum of the 5 group counts of the groups the centre belongs
+// to (Fig. 1), weighs the centre 5 times, its 4 nearest neighbours and 4 diagonal neighbours
+// twice, and the 4 sites two steps away along the axes once (a neighbour w of z lies in z's own
+// group and in w's; a diagonal site in the groups of the two neighbours it shares with z; an axis
+// site at distance 2 in the group of the neighbour between them).
+constexpr uint32_t kOnesLo = (1u << 11) | (1u << 25) | (1u << 29);    // (-2, 0), (0, -2), (0, +2)
+constexpr uint32_t kOnesHi = 1u << (43 - 32);                         // (+2, 0)
+constexpr uint32_t kTwosLo = (1u << 18) | (1u << 19) | (1u << 20) | (1u << 26) | (1u << 28);
+constexpr uint32_t kTwosHi = (1u << (34 - 32)) | (1u << (35 - 32)) | (1u << (36 - 32));  // row +1
 // the 4 nearest neighbours alone (the pairwise game's cooperating neighbours, Section VI)
-constexpr uint32_t kNearLo = (1u << 17) | (1u << 23) | (1u << 25) | (1u << 31);
+constexpr uint32_t kNearLo = (1u << 19) | (1u << 26) | (1u << 28);
+constexpr uint32_t kNearHi = 1u << (35 - 32);
 
 struct Ctx {
     uint32_t *rows;                       // band + halo rows (local row lr = global row r0 - H + lr)
@@ -155,6 +141,8 @@ struct Ctx {
     uint32_t cmagic;                      // ceil(2^16 / cpr): floor(k / cpr) = (k cmagic) >> 16 for small k
     long long n_words;                    // words of band + halo rows (checked build)
     int *status;
+    uint64_t k;                           // sublattice step index
+    int oj;                               // column offset of the step's sublattice (0..3)
 };
 
 // The adoption decision of one active site: entry = local row << 18 | column << 2 | direction
@@ -172,7 +160,7 @@ __device__ __forceinline__ uint32_t site_flip(const Ctx &cx, uint32_t e, int &wo
     uint4 u4 = make_uint4(static_cast<uint32_t>(j >> 4), static_cast<uint32_t>(i >> 2), cx.kl, cx.kh_u);
 #pragma unroll
     for (int r = 0; r < 10; ++r) philox_round(u4, cx.rk->k0[r], cx.rk->k1[r]);
-    // columns j - 3 .. j + 3 of rows lr - 3 .. lr + 3, from the two words holding them
+    // columns j - 3 .. j + 4 of rows lr - 3 .. lr + 3, from the two words holding them
     const int c0 = j >= 3 ? j - 3 : j - 3 + cx.L;
     const int wa = c0 >> 5, wb = wa + 1 == cx.Lw ? 0 : wa + 1, sh = c0 & 31;
     constexpr int q0 = 3 - kReadRadius<GAME>;  // the rows the game reads: q0 .. 6 - q0
@@ -184,21 +172,22 @@ __device__ __forceinline__ uint32_t site_flip(const Ctx &cx, uint32_t e, int &wo
         const long long ra = static_cast<long long>(lr - 3 + q) * cx.Lw;
         v[q] = (q >= q0 && q <= 6 - q0 && index_ok(ra + swz(wa), cx.n_words, cx.status) &&
                 index_ok(ra + swz(wb), cx.n_words, cx.status))
-                   ? (__funnelshift_r(pa[(q - q0) * cx.Lw], pb[(q - q0) * cx.Lw], sh) & 0x7Fu)
+                   ? __funnelshift_r(pa[(q - q0) * cx.Lw], pb[(q - q0) * cx.Lw], sh)
                    : 0u;
     }
-    const uint32_t lo = v[0] | v[1] << 7 | v[2] << 14 | v[3] << 21 | v[4] << 28;
-    const uint32_t hi = v[4] >> 4 | v[5] << 3 | v[6] << 10;
-    const uint32_t sx = (v[3] >> 3) & 1u;
-    // the same bits centred on y: shifted right for y to the right (+1) or below (+7), left otherwise
-    const uint32_t rs = d == 0 ? 1u : (d == 2 ? 7u : 0u);
-    const uint32_t ls = d == 1 ? 1u : (d == 3 ? 7u : 0u);
+    // the rows' low bytes side by side: lo = rows 0..3, hi = rows 4..6 (its top byte is not used)
+    const uint32_t lo = __byte_perm(__byte_perm(v[0], v[1], 0x0040u), __byte_perm(v[2], v[3], 0x0040u), 0x5410u);
+    const uint32_t hi = __byte_perm(__byte_perm(v[4], v[5], 0x0040u), v[6], 0x0410u);
+    const uint32_t sx = (lo >> 27) & 1u;
+    // the same bits centred on y: shifted right for y to the right (+1) or below (+8), left otherwise
+    const uint32_t rs = d == 0 ? 1u : (d == 2 ? 8u : 0u);
+    const uint32_t ls = d == 1 ? 1u : (d == 3 ? 8u : 0u);
     uint32_t ylo = __funnelshift_r(lo, hi, rs), yhi = hi >> rs;
     yhi = __funnelshift_l(ylo, yhi, ls);
     ylo <<= ls;
     uint32_t idx;
     if constexpr (GAME == kPairGame) {
-        const uint32_t nx = __popc(lo & kNearLo), ny = __popc(ylo & kNearLo);
+        const uint32_t nx = __popc(lo & kNearLo) + __popc(hi & kNearHi), ny = __popc(ylo & kNearLo) + __popc(yhi & kNearHi);
         idx = (sx * 5u + nx) * 5u + ny;
     } else {
         const uint32_t Sx = __popc(lo & kOnesLo) + __popc(hi & kOnesHi) +
@@ -224,6 +213,7 @@ struct Rings {
     uint2 *words;
     uint32_t *sites;
     uint32_t wh, wt, sh, st;  // heads and tails (warp-uniform)
+    uint32_t flips;           // adoptions this thread made in the current step
 };
 
 // Warp-uniform: update the next n (<= 64) active sites, two per lane (sites lane and lane + 32).
@@ -239,10 +229,12 @@ __device__ __forceinline__ void drain_sites(const Ctx &cx, Rings &q, uint32_t n,
         const uint32_t f1 = site_flip<GAME>(cx, q.sites[(q.sh + l + 32u) & kSiteRingMask], a1);
         if (f0) atomicXor(&cx.rows[a0], f0);
         if (f1) atomicXor(&cx.rows[a1], f1);
+        q.flips += (f0 != 0u) + (f1 != 0u);
     } else if (l < n) {
         int a0;
         const uint32_t f0 = site_flip<GAME>(cx, q.sites[(q.sh + l) & kSiteRingMask], a0);
         if (f0) atomicXor(&cx.rows[a0], f0);
+        q.flips += f0 != 0u;
     }
     q.sh += n;
 }
@@ -251,7 +243,7 @@ __device__ __forceinline__ void drain_sites(const Ctx &cx, Rings &q, uint32_t n,
 // ring positions from a prefix sum of the lanes' site counts, <= 8, by its bits), then update
 // sites while 64 or more are waiting. The site ring holds < 64 entries before and at most
 // 63 + 256 after.
-template <int OJ, int GAME>
+template <int GAME>
 __device__ __forceinline__ void expand_words(const Ctx &cx, Rings &q, uint32_t n, int lane) {
     __syncwarp();
     uint32_t act = 0, y = 0;
@@ -267,7 +259,7 @@ __device__ __forceinline__ void expand_words(const Ctx &cx, Rings &q, uint32_t n
     uint32_t pos = q.st + __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt) + 8u * __popc(b3 & lt);
     q.st += __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2) + 8u * __popc(b3);
     const uint32_t d16 = y & 0xFFFFu;
-    const uint32_t ebase = (y >> 25) << 18 | (32u * ((y >> 16) & 0x1FFu) + OJ) << 2;
+    const uint32_t ebase = (y >> 25) << 18 | (32u * ((y >> 16) & 0x1FFu) + static_cast<uint32_t>(cx.oj)) << 2;
     while (act) {
         const int m = (__ffs(act) - 1) >> 2;
         q.sites[pos & kSiteRingMask] = ebase + (static_cast<uint32_t>(4 * m) << 2) + ((d16 >> (2 * m)) & 3u);
@@ -277,27 +269,28 @@ __device__ __forceinline__ void expand_words(const Ctx &cx, Rings &q, uint32_t n
     while (q.st - q.sh >= 64u) drain_sites<GAME>(cx, q, 64u, lane);
 }
 
-// Activity of the 8 sites of one word (nibble bits): s_x != s_y for the drawn neighbour y. l, c, r:
+// Activity of the 8 sites of one word (nibble bits): s_x != s_y for the drawn neighbour y; oj: the
+// sublattice's column offset. l, c, r:
 // the word and its left and right neighbours in the site's row; uc, ur / dc, dr: the word and
 // its right neighbour in the rows above / below; d16: the sites' direction codes.
-template <int OJ>
-__device__ __forceinline__ uint32_t word_activity(uint32_t l, uint32_t c, uint32_t r, uint32_t uc, uint32_t ur,
+__device__ __forceinline__ uint32_t word_activity(int oj, uint32_t l, uint32_t c, uint32_t r, uint32_t uc, uint32_t ur,
                                                   uint32_t dc, uint32_t dr, uint32_t d16) {
     uint32_t dd = d16;
     dd = (dd | (dd << 8)) & 0x00FF00FFu;
     dd = (dd | (dd << 4)) & 0x0F0F0F0Fu;
     dd = (dd | (dd << 2)) & 0x33333333u;
     const uint32_t lo_b = dd & kNib, hi_b = (dd >> 1) & kNib;
-    const uint32_t sx = window<OJ>(l, c, r) & kNib;
-    const uint32_t ye = window<OJ + 1>(l, c, r) & kNib;
-    const uint32_t yw = window<OJ - 1>(l, c, r) & kNib;
-    const uint32_t ys = window<OJ>(0u, dc, dr) & kNib;
-    const uint32_t yn = window<OJ>(0u, uc, ur) & kNib;
+    // columns oj + 4m + D of the three rows (a shift of 0 returns the word itself)
+    const uint32_t sx = __funnelshift_r(c, r, oj) & kNib;
+    const uint32_t ye = __funnelshift_r(c, r, oj + 1) & kNib;
+    const uint32_t yw = (oj ? __funnelshift_r(c, r, oj - 1) : __funnelshift_l(l, c, 1)) & kNib;
+    const uint32_t ys = __funnelshift_r(dc, dr, oj) & kNib;
+    const uint32_t yn = __funnelshift_r(uc, ur, oj) & kNib;
     return sx ^ mux(hi_b, mux(lo_b, ye, yw), mux(lo_b, ys, yn));
 }
 
 // Warp-uniform: append the lanes' active words to the word ring; expand 32 when they are there.
-template <int OJ, int GAME>
+template <int GAME>
 __device__ __forceinline__ void push_word(const Ctx &cx, Rings &q, uint32_t act, int lr, int w, uint32_t d16,
                                           int lane) {
     const uint32_t bal = __ballot_sync(0xffffffffu, act != 0u);
@@ -305,7 +298,7 @@ __device__ __forceinline__ void push_word(const Ctx &cx, Rings &q, uint32_t act,
         q.words[(q.wt + __popc(bal & ((1u << lane) - 1u))) & kWordRingMask] =
             make_uint2(act, static_cast<uint32_t>(lr) << 25 | static_cast<uint32_t>(w) << 16 | d16);
     q.wt += __popc(bal);
-    if (q.wt - q.wh >= 32u) expand_words<OJ, GAME>(cx, q, 32u, lane);
+    if (q.wt - q.wh >= 32u) expand_words<GAME>(cx, q, 32u, lane);
 }
 
 // Sublattice rows (local lr = first + 4 k, k < n) of a step.
@@ -322,6 +315,61 @@ __device__ __forceinline__ Range srows_in(int m4, int lo, int hi) {
     return r;
 }
 
+// One 64-word chunk of a sublattice row as a lane sees it: its two words, their neighbours and
+// their direction bits.
+struct Chunk {
+    int lr, wa;
+    bool valid;
+    uint32_t d32, cl, ca, cb, cq, ua, ub, uq, da, db, dq;
+};
+
+// The direction draws of a warp's next 4 chunks: lane l computes call l mod 8 of chunk o + l / 8
+// (row lr2, column chunk c2; `have` false: past the warp's last chunk).
+__device__ __forceinline__ void direction_calls(const Ctx &cx, uint4 &dcall, bool have, int lr2, int c2, int lane) {
+    uint32_t g = 0, a = 0;
+    if (have) {
+        int i2 = cx.r0 - cx.H + lr2;
+        if (i2 < 0) i2 += cx.L;
+        else if (i2 >= cx.L) i2 -= cx.L;
+        g = static_cast<uint32_t>(8 * c2 + (lane & 7));
+        a = static_cast<uint32_t>(i2 >> 2);
+    }
+    dcall = make_uint4(g, a, cx.kl, cx.kh_dir);
+#pragma unroll
+    for (int rr = 0; rr < 10; ++rr) philox_round(dcall, cx.rk->k0[rr], cx.rk->k1[rr]);
+}
+
+// Load chunk (row ch.lr, column chunk c) of the warp's chunk ordinal o: words w0 = 64 c + 2 lane
+// and w0 + 1. Their 32 direction bits are word lane mod 4 of call (chunk o, lane / 4), which
+// lane 8 (o mod 4) + lane / 4 holds.
+__device__ __forceinline__ void load_chunk(const Ctx &cx, const uint4 &dcall, int o, int c, int lane, Chunk &ch) {
+    const int src = 8 * (o & 3) + (lane >> 2);
+    const uint32_t dx = __shfl_sync(0xffffffffu, dcall.x, src), dy = __shfl_sync(0xffffffffu, dcall.y, src);
+    const uint32_t dz = __shfl_sync(0xffffffffu, dcall.z, src), dw = __shfl_sync(0xffffffffu, dcall.w, src);
+    const int comp = lane & 3;
+    ch.d32 = comp == 0 ? dx : comp == 1 ? dy : comp == 2 ? dz : dw;
+    const int w0 = 64 * c + 2 * lane;
+    ch.valid = w0 < cx.Lw;  // Lw is even, so w0 + 1 is valid with w0
+    ch.wa = ch.valid ? w0 : 0;
+    const int wa = ch.wa;
+    const int wp = wa == 0 ? cx.Lw - 1 : wa - 1, wb = wa + 1, wq = wa + 2 == cx.Lw ? 0 : wa + 2;
+    const long long rb = static_cast<long long>(ch.lr - 1) * cx.Lw;
+    const uint32_t *row = cx.rows + (ch.lr - 1) * cx.Lw;
+#define PGG_LD(RR, WW) \
+    (index_ok(rb + (RR) * cx.Lw + swz(WW), cx.n_words, cx.status) ? row[(RR) * cx.Lw + swz(WW)] : 0u)
+    ch.cl = PGG_LD(1, wp);
+    ch.ca = PGG_LD(1, wa);
+    ch.cb = PGG_LD(1, wb);
+    ch.cq = PGG_LD(1, wq);
+    ch.ua = PGG_LD(0, wa);
+    ch.ub = PGG_LD(0, wb);
+    ch.uq = cx.oj > 0 ? PGG_LD(0, wq) : 0u;
+    ch.da = PGG_LD(2, wa);
+    ch.db = PGG_LD(2, wb);
+    ch.dq = cx.oj > 0 ? PGG_LD(2, wq) : 0u;
+#undef PGG_LD
+}
+
 // Scan the rows of up to three ranges in chunks of 64 words, two consecutive words per lane;
 // chunk K of the ranges' concatenation goes to warp K mod 16, so the warps get equal shares.
 // Before its first chunk in range wait_at or later the warp waits for the halo (`wait` returns
@@ -329,7 +377,7 @@ __device__ __forceinline__ Range srows_in(int m4, int lo, int hi) {
 // warp's word ring, and 32 of them at a time to the site ring. The direction draws of a warp's
 // next 4 chunks come from one Philox call per lane (chunk o + lane / 8, call lane mod 8 of the
 // chunk's 8) and reach the lanes that use them by shuffles. Warp-uniform.
-template <int OJ, int GAME, class Wait>
+template <int GAME, class Wait>
 __device__ __forceinline__ bool scan_step(const Ctx &cx, const Range (&rg)[3], int wait_at, Wait wait, Rings &q,
                                           int warp, int lane) {
     const int cpr = cx.cpr;
@@ -352,53 +400,37 @@ __device__ __forceinline__ bool scan_step(const Ctx &cx, const Range (&rg)[3], i
         lr = (r == 0 ? rg[0].first : r == 1 ? rg[1].first : rg[2].first) + 4 * qr;  // no indexed array
         return r;
     };
+    // two chunks per iteration (this warp's chunks o and o + 1): their loads and activity chains are
+    // independent, which gives the scheduler two chains per warp to interleave
     int o = 0;
-    for (int K = warp; K < total; K += kComputeWarps, ++o) {
-        int lr, c;
-        const int r = locate(K, lr, c);
-        if (!waited && r >= wait_at) {
+    for (int K = warp; K < total; K += 2 * kComputeWarps, o += 2) {
+        const bool two = K + kComputeWarps < total;
+        Chunk A, B;
+        int cA, cB = 0;
+        const int rA = locate(K, A.lr, cA);
+        const int rB = two ? locate(K + kComputeWarps, B.lr, cB) : rA;
+        if (!two) B.lr = A.lr;
+        if (!waited && (rA >= wait_at || rB >= wait_at)) {
             if (!wait()) return false;
             waited = true;
         }
         if ((o & 3) == 0) {
             const int K2 = K + kComputeWarps * (lane >> 3);
-            uint32_t g = 0, a = 0;
-            if (K2 < total) {
-                int lr2, c2;
-                locate(K2, lr2, c2);
-                int i2 = cx.r0 - cx.H + lr2;
-                if (i2 < 0) i2 += cx.L;
-                else if (i2 >= cx.L) i2 -= cx.L;
-                g = static_cast<uint32_t>(8 * c2 + (lane & 7));
-                a = static_cast<uint32_t>(i2 >> 2);
-            }
-            dcall = make_uint4(g, a, cx.kl, cx.kh_dir);
-#pragma unroll
-            for (int rr = 0; rr < 10; ++rr) philox_round(dcall, cx.rk->k0[rr], cx.rk->k1[rr]);
+            int lr2 = 0, c2 = 0;
+            if (K2 < total) locate(K2, lr2, c2);
+            direction_calls(cx, dcall, K2 < total, lr2, c2, lane);
         }
-        // words w0 = 64 c + 2 lane and w0 + 1: their 32 direction bits are word lane mod 4 of call
-        // (chunk o, lane / 4), which lane 8 (o mod 4) + lane / 4 holds
-        const int src = 8 * (o & 3) + (lane >> 2);
-        const uint32_t dx = __shfl_sync(0xffffffffu, dcall.x, src), dy = __shfl_sync(0xffffffffu, dcall.y, src);
-        const uint32_t dz = __shfl_sync(0xffffffffu, dcall.z, src), dw = __shfl_sync(0xffffffffu, dcall.w, src);
-        const int comp = lane & 3;
-        const uint32_t d32 = comp == 0 ? dx : comp == 1 ? dy : comp == 2 ? dz : dw;
-        const int w0 = 64 * c + 2 * lane;
-        const bool valid = w0 < cx.Lw;  // Lw is even, so w0 + 1 is valid with w0
-        const int wa = valid ? w0 : 0;
-        const int wp = wa == 0 ? cx.Lw - 1 : wa - 1, wb = wa + 1, wq = wa + 2 == cx.Lw ? 0 : wa + 2;
-        const long long rb = static_cast<long long>(lr - 1) * cx.Lw;
-        const uint32_t *row = cx.rows + (lr - 1) * cx.Lw;
-        auto ld = [&](int rr, int ww) -> uint32_t {
-            return index_ok(rb + rr * cx.Lw + swz(ww), cx.n_words, cx.status) ? row[rr * cx.Lw + swz(ww)] : 0u;
-        };
-        const uint32_t cl = ld(1, wp), ca = ld(1, wa), cb = ld(1, wb), cq = ld(1, wq);
-        const uint32_t ua = ld(0, wa), ub = ld(0, wb), uq = OJ > 0 ? ld(0, wq) : 0u;
-        const uint32_t da = ld(2, wa), db = ld(2, wb), dq = OJ > 0 ? ld(2, wq) : 0u;
-        const uint32_t act0 = valid ? word_activity<OJ>(cl, ca, cb, ua, ub, da, db, d32 & 0xFFFFu) : 0u;
-        const uint32_t act1 = valid ? word_activity<OJ>(ca, cb, cq, ub, uq, db, dq, d32 >> 16) : 0u;
-        push_word<OJ, GAME>(cx, q, act0, lr, wa, d32 & 0xFFFFu, lane);
-        push_word<OJ, GAME>(cx, q, act1, lr, wb, d32 >> 16, lane);
+        load_chunk(cx, dcall, o, cA, lane, A);
+        load_chunk(cx, dcall, o + 1, two ? cB : cA, lane, B);
+        if (!two) B.valid = false;
+        const uint32_t a0 = A.valid ? word_activity(cx.oj, A.cl, A.ca, A.cb, A.ua, A.ub, A.da, A.db, A.d32 & 0xFFFFu) : 0u;
+        const uint32_t a1 = A.valid ? word_activity(cx.oj, A.ca, A.cb, A.cq, A.ub, A.uq, A.db, A.dq, A.d32 >> 16) : 0u;
+        const uint32_t b0 = B.valid ? word_activity(cx.oj, B.cl, B.ca, B.cb, B.ua, B.ub, B.da, B.db, B.d32 & 0xFFFFu) : 0u;
+        const uint32_t b1 = B.valid ? word_activity(cx.oj, B.ca, B.cb, B.cq, B.ub, B.uq, B.db, B.dq, B.d32 >> 16) : 0u;
+        push_word<GAME>(cx, q, a0, A.lr, A.wa, A.d32 & 0xFFFFu, lane);
+        push_word<GAME>(cx, q, a1, A.lr, A.wa + 1, A.d32 >> 16, lane);
+        push_word<GAME>(cx, q, b0, B.lr, B.wa, B.d32 & 0xFFFFu, lane);
+        push_word<GAME>(cx, q, b1, B.lr, B.wa + 1, B.d32 >> 16, lane);
     }
     // every warp sees the halo load complete before the step ends, even one without a chunk that
     // reads it: the communication warp reuses the mbarrier, the halo rows and the neighbours'
@@ -408,15 +440,103 @@ __device__ __forceinline__ bool scan_step(const Ctx &cx, const Range (&rg)[3], i
 }
 
 // All remaining active words and sites of the warp. Warp-uniform.
-template <int OJ, int GAME>
+template <int GAME>
 __device__ __forceinline__ void flush_rings(const Ctx &cx, Rings &q, int lane) {
-    if (q.wt != q.wh) expand_words<OJ, GAME>(cx, q, q.wt - q.wh, lane);
+    if (q.wt != q.wh) expand_words<GAME>(cx, q, q.wt - q.wh, lane);
     while (q.st != q.sh) drain_sites<GAME>(cx, q, min(64u, q.st - q.sh), lane);
+}
+
+// The dense pass: every word of the rows, all 8 sites at once by the shared per-word core
+// (pgg_unit.cuh): tasks of tw words of one sublattice row per thread, the 7 x 3 neighbourhood
+// slid along the row, one direction call per task. It pays for every word, active or not, and so
+// wins over the scan when a large share of the sites can change (early MCS from a random start,
+// high cooperator densities).
+//
+// Task t goes to thread (first + t) mod T, so that a range that follows another starts at the
+// threads the previous one left one task short. Returns the number of tasks.
+template <int OJ, int GAME>
+__device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int tid, int first, uint32_t &flips) {
+    if (rg.n <= 0) return 0;
+    const int words = rg.n * cx.Lw;
+    const int tw = words >= 4 * kComputeThreads ? 4 : words >= 2 * kComputeThreads ? 2 : 1;
+    const int runs = cx.Lw / tw;  // Lw % 8 == 0, so tasks never straddle a direction call
+    const int n_tasks = rg.n * runs;
+    const uint32_t kh = static_cast<uint32_t>(cx.k >> 32) | kTagDir;
+    int t0 = tid - first % kComputeThreads;
+    if (t0 < 0) t0 += kComputeThreads;
+    for (int t = t0; t < n_tasks; t += kComputeThreads) {
+        const int qr = t / runs;
+        const int w0 = (t - qr * runs) * tw;
+        const int lr = rg.first + 4 * qr;
+        int i = cx.r0 - cx.H + lr;
+        if (i < 0) i += cx.L;
+        else if (i >= cx.L) i -= cx.L;
+        const int wprev = w0 == 0 ? cx.Lw - 1 : w0 - 1;
+        uint32_t wl[7], wc[7], wr[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const long long base = static_cast<long long>(lr - 3 + q) * cx.Lw;
+            const bool rd = reads_row<GAME>(q);
+            wl[q] = rd && index_ok(base + swz(wprev), cx.n_words, cx.status) ? cx.rows[base + swz(wprev)] : 0u;
+            wc[q] = rd && index_ok(base + swz(w0), cx.n_words, cx.status) ? cx.rows[base + swz(w0)] : 0u;
+        }
+        const uint4 dcall = philox_rk(make_uint4(static_cast<uint32_t>(w0 >> 3), static_cast<uint32_t>(i >> 2), cx.kl, kh), *cx.rk);
+        UnitCtx u;
+        u.k = cx.k;
+        u.a = static_cast<uint32_t>(i >> 2);
+        u.msk = kNib;
+#pragma unroll 1
+        for (int w = w0; w < w0 + tw; ++w) {
+            const int wn = w + 1 == cx.Lw ? 0 : w + 1;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const long long base = static_cast<long long>(lr - 3 + q) * cx.Lw;
+                wr[q] = reads_row<GAME>(q) && index_ok(base + swz(wn), cx.n_words, cx.status) ? cx.rows[base + swz(wn)] : 0u;
+            }
+            u.gw = w;
+            u.d16 = (word_of(dcall, (w >> 1) & 3) >> (16 * (w & 1))) & 0xFFFFu;
+            uint32_t sx;
+            const uint32_t f = game_flips<OJ, GAME>(wl, wc, wr, u, *cx.rk, cx.table, sx);
+            // one thread owns the word in this pass: a plain store (the bits other threads read
+            // from it are never among the flipped ones)
+            if (f && index_ok(static_cast<long long>(lr) * cx.Lw + swz(w), cx.n_words, cx.status))
+                cx.rows[lr * cx.Lw + swz(w)] = wc[3] ^ (f << OJ);
+            flips += __popc(f);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                wl[q] = wc[q];
+                wc[q] = wr[q];
+            }
+        }
+    }
+    return n_tasks;
+}
+
+// One step of the dense pass (the rows and the halo wait as in step_rows).
+template <int OJ, int GAME, class Wait>
+__device__ __forceinline__ bool step_dense(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
+                                           int tid, uint32_t &flips) {
+    constexpr int R = kReadRadius<GAME>;
+    const int in_lo = cx.H + R, in_hi = cx.H + nb - R;
+    if (!split) {
+        dense_rows<OJ, GAME>(cx, srows_in(m4, lo, hi), tid, 0, flips);
+        return true;
+    }
+    int next = 0;
+    if (in_hi > in_lo) next = dense_rows<OJ, GAME>(cx, srows_in(m4, in_lo, in_hi), tid, 0, flips);
+    if (!wait()) return false;
+    if (in_hi > in_lo) {
+        next += dense_rows<OJ, GAME>(cx, srows_in(m4, lo, in_lo), tid, next, flips);
+        dense_rows<OJ, GAME>(cx, srows_in(m4, in_hi, hi), tid, next, flips);
+    } else {
+        dense_rows<OJ, GAME>(cx, srows_in(m4, lo, hi), tid, 0, flips);
+    }
+    return true;
 }
 
 // One step: with `split`, first the rows whose reads stay inside the band, then -- once the
 // halo has landed -- the rest; then every remaining active site.
-template <int OJ, int GAME, class Wait>
+template <int GAME, class Wait>
 __device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
                                           Rings &q, int warp, int lane) {
     constexpr int R = kReadRadius<GAME>;
@@ -435,8 +555,8 @@ __device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi,
         rg[2] = srows_in(m4, in_hi, hi);
         wait_at = 1;
     }
-    if (!scan_step<OJ, GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
-    flush_rings<OJ, GAME>(cx, q, lane);
+    if (!scan_step<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
+    flush_rings<GAME>(cx, q, lane);
     return true;
 }
 
@@ -518,6 +638,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ volatile int s_abort;
     __shared__ unsigned long long s_warp[kComputeWarps];
+    __shared__ unsigned int s_flips[3];  // adoptions in the CTA's steps j (mod 3)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool comm = tid >= kComputeThreads;  // the last warp exchanges halos, the others compute
     const int up = (b + nbnd - 1) % nbnd, down = (b + 1) % nbnd;
@@ -534,6 +655,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     if (tid == 0) {
         s_abort = 0;
         mbar_init(&s_mbar, 1);
+        // the step before the first one: the adoptions the band saw in the last step of the
+        // previous launch (a hint for the first pass; it never affects results)
+        s_flips[2] = p.hint ? p.hint[b] : 0u;
+        s_flips[0] = 0u;
+        s_flips[1] = 0u;
     }
     // stage band + halo (rows r0 - H .. r0 + nb + H - 1, periodic) with 4-byte asynchronous
     // copies (cp.async: many loads in flight per thread, each word to its place); thread t
@@ -585,6 +711,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     q.words = s_wring + (warp < kComputeWarps ? warp : 0) * kWordRingCap;
     q.sites = s_sring + (warp < kComputeWarps ? warp : 0) * kSiteRingCap;
     q.wh = q.wt = q.sh = q.st = 0;
+    // the dense pass takes a step when the previous step flipped more than this many sites of the
+    // band (a share of the sites one step updates)
+    const unsigned int dense_above =
+        static_cast<unsigned int>((static_cast<unsigned long long>(nb) * L / 16) * p.dense_per_mille / 1000);
     uint4 ocall = make_uint4(0, 0, 0, 0);
     uint64_t ocall_idx = ~0ull;
     const int n_blocks = 16 * p.n_mcs / S;
@@ -626,6 +756,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 }
                 const int o = static_cast<int>((word_of(ocall, static_cast<int>((k >> 3) & 3)) >> (4 * (k & 7))) & 15u);
                 cx.kl = static_cast<uint32_t>(k);
+                cx.k = k;
+                cx.oj = o & 3;
                 cx.kh_dir = static_cast<uint32_t>(k >> 32) | kTagDir;
                 cx.kh_u = static_cast<uint32_t>(k >> 32) | kTagU;
                 // local row lr is global row r0 - H + lr: a sublattice row iff lr = oi - r0 + H (mod 4)
@@ -640,13 +772,23 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                     }
                     return true;
                 };
+                if (tid == 0) s_flips[(j + 1) % 3] = 0u;  // the slot of step j + 1 (last read in step j - 1)
+                const bool dense = s_flips[(j + 2) % 3] > dense_above;  // the previous step's adoptions
+                q.flips = 0;
                 bool ok = true;
-                switch (o & 3) {
-                    case 0: ok = step_rows<0, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
-                    case 1: ok = step_rows<1, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
-                    case 2: ok = step_rows<2, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
-                    default: ok = step_rows<3, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane); break;
+                if (dense) {
+                    switch (o & 3) {
+                        case 0: ok = step_dense<0, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        case 1: ok = step_dense<1, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        case 2: ok = step_dense<2, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        default: ok = step_dense<3, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                    }
+                } else {
+                    ok = step_rows<GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane);
                 }
+                // the step's adoptions, for the next step's choice of pass
+                const unsigned int wf = __reduce_add_sync(0xffffffffu, q.flips);
+                if (lane == 0 && wf) atomicAdd(&s_flips[j % 3], wf);
                 if (!ok) {
                     s_abort = 1;
                     q.wh = q.wt;  // the step is abandoned
@@ -718,6 +860,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
         }
     }
     __syncthreads();  // the last bulk store has completed (its issuer waited) before the band is stored
+    if (tid == 0 && p.hint) p.hint[b] = s_flips[(16 * p.n_mcs - 1) % 3];
     // store the band (the same column-per-thread walk)
     if (row_first < rows_per_pass) {
         if (p.lat8) {
@@ -800,6 +943,8 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.counts = a.counts;
     p.status = a.status;
     p.spin_limit = a.spin_limit;
+    p.hint = a.hint;
+    p.dense_per_mille = a.dense_per_mille;
     p.rk = philox_round_keys(a.seed);
     const size_t smem = resident_smem_bytes(a.L, a.n_bands, a.game, p.s);
     const void *kernel = a.game == kPairGame ? reinterpret_cast<const void *>(k_resident<kPairGame>)

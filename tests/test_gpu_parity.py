@@ -434,6 +434,25 @@ def test_resident_steps_per_exchange(o, pgg, L, spe, n_mcs, layout):
     assert np.array_equal(got_lat, want_lat)
 
 
+@pytest.mark.parametrize("spe", [1, 4])
+def test_resident_dense_and_sparse_passes(o, pgg, spe):
+    """A random half-and-half lattice (most sites can change: the dense pass) and a lattice of a
+    few cooperator discs in a defector sea (few boundary sites: the pass over active sites only),
+    each run for several MCS in one call and in calls of one MCS (the pass is chosen per step from
+    the previous step's adoptions, across launches too), against the oracle."""
+    L = 2048
+    for lat0 in (inputs.random_lattice(L, 0.5, seed=71), inputs.clustered_lattice(L, 12, 20, seed=72)):
+        ref = lat0.copy()
+        want = o.run(ref, 3.8, 0.5, 13, 16 * 3, 4, threads=THREADS)
+        with pgg.Lattice(L, 3.8, 0.5, layout="bitpack") as lat:
+            lat.set_schedule("resident", 16, 0, spe)
+            lat.seed(13)
+            lat.set(lat0, 16 * 3)
+            got = np.concatenate([lat.step_mcs(2), lat.step_mcs(1), lat.step_mcs(1)])
+            final, _ = lat.get()
+        assert np.array_equal(got, want) and np.array_equal(final, ref)
+
+
 def test_resident_steps_per_exchange_limits(pgg):
     """Steps per exchange: 1, 2 or 4, and only as many as the bands' rows and the shared memory
     allow (bands of 6-7 rows at L = 1024 take at most 2); the default is the largest that fits."""
