@@ -39,18 +39,20 @@ FALLBACK_HBM_GBS = 6800.0
 # ALU pipe / of the FMA-heavy pipe (integer multiply-adds), dram_bytes = dram__bytes_read.sum +
 # dram__bytes_write.sum.
 NCU = {
+    # the resident kernel (active-site and dense passes): means of 9 launches inside the timed window
+    # (MCS 5-7, 13-15, 22-24 of the benchmark command with --no-autotune and the schedule named)
+    "resident:a7143b361679422b:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 33654745, "fma_warp_inst": 25207800, "dram_bytes": 8517831},
+    "resident:a7143b361679422b:bitpack:8192:16:152:2":
+        {"alu_warp_inst": 34502755, "fma_warp_inst": 25948627, "dram_bytes": 8517945},
+    "resident:a7143b361679422b:bitpack:8192:16:152:4":
+        {"alu_warp_inst": 36973461, "fma_warp_inst": 27714790, "dram_bytes": 8524288},
+    "resident-pairwise:a7143b361679422b:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 45525243, "fma_warp_inst": 31211273, "dram_bytes": 8532708},
+    "resident:a7143b361679422b:u8:8192:16:152:2":
+        {"alu_warp_inst": 37148052, "fma_warp_inst": 27578378, "dram_bytes": 81858788},
     "direct:1385c7b1fc7d18a3:bitpack:8192:1:4:64":
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
-    # mean of 9 launches inside the timed window (MCS 5-7, 13-15, 22-24 of the default run)
-    "resident:4553e3e27d196ddf:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 55944145, "fma_warp_inst": 44618532, "dram_bytes": 8485006},
-    "resident:59b615d25f4199b1:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 56250783, "fma_warp_inst": 44529750, "dram_bytes": 8485376},
-    # a uint8 context runs the same kernel, staging and writing back the uint8 lattice itself
-    "resident:59b615d25f4199b1:u8:8192:16:152:0":
-        {"alu_warp_inst": 58792335, "fma_warp_inst": 46059208, "dram_bytes": 79408640},
-    "resident-pairwise:59b615d25f4199b1:bitpack:8192:16:152:0":
-        {"alu_warp_inst": 44228756, "fma_warp_inst": 29225428, "dram_bytes": 8470784},
 }
 
 # Integer ALU pipe of one SM: 4 sub-partitions x 16 lanes per clock (half-rate pipe).
