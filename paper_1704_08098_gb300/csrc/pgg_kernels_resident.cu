@@ -458,7 +458,10 @@ template <int OJ, int GAME>
 __device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int tid, int first, uint32_t &flips) {
     if (rg.n <= 0) return 0;
     const int words = rg.n * cx.Lw;
-    const int tw = words >= 4 * kComputeThreads ? 4 : words >= 2 * kComputeThreads ? 2 : 1;
+    // words per task: as many as still give every thread of the round a task; a range that starts
+    // mid-round (first > 0) sizes its tasks for the threads that round leaves free
+    const int free_thr = kComputeThreads - first % kComputeThreads;
+    const int tw = words >= 4 * free_thr ? 4 : words >= 2 * free_thr ? 2 : 1;
     const int runs = cx.Lw / tw;  // Lw % 8 == 0, so tasks never straddle a direction call
     const int n_tasks = rg.n * runs;
     const uint32_t kh = static_cast<uint32_t>(cx.k >> 32) | kTagDir;
