@@ -41,16 +41,16 @@ FALLBACK_HBM_GBS = 6800.0
 NCU = {
     # the resident kernel (active-site and dense passes): means of 9 launches inside the timed window
     # (MCS 5-7, 13-15, 22-24 of the benchmark command with --no-autotune and the schedule named)
-    "resident:a7143b361679422b:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 33654745, "fma_warp_inst": 25207800, "dram_bytes": 8517831},
-    "resident:a7143b361679422b:bitpack:8192:16:152:2":
-        {"alu_warp_inst": 34502755, "fma_warp_inst": 25948627, "dram_bytes": 8517945},
-    "resident:a7143b361679422b:bitpack:8192:16:152:4":
-        {"alu_warp_inst": 36973461, "fma_warp_inst": 27714790, "dram_bytes": 8524288},
-    "resident-pairwise:a7143b361679422b:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 45525243, "fma_warp_inst": 31211273, "dram_bytes": 8532708},
-    "resident:a7143b361679422b:u8:8192:16:152:2":
-        {"alu_warp_inst": 37148052, "fma_warp_inst": 27578378, "dram_bytes": 81858788},
+    "resident:9f87374f47ba399d:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 33660172, "fma_warp_inst": 25270637, "dram_bytes": 8520590},
+    "resident:9f87374f47ba399d:bitpack:8192:16:152:2":
+        {"alu_warp_inst": 34504090, "fma_warp_inst": 26006604, "dram_bytes": 8518059},
+    "resident:9f87374f47ba399d:bitpack:8192:16:152:4":
+        {"alu_warp_inst": 36979227, "fma_warp_inst": 27781282, "dram_bytes": 8526080},
+    "resident-pairwise:9f87374f47ba399d:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 45537800, "fma_warp_inst": 31139998, "dram_bytes": 8533276},
+    "resident:9f87374f47ba399d:u8:8192:16:152:2":
+        {"alu_warp_inst": 37148059, "fma_warp_inst": 27635636, "dram_bytes": 81858446},
     "direct:1385c7b1fc7d18a3:bitpack:8192:1:4:64":
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
 }
@@ -405,9 +405,6 @@ def main():
         tuned = lat.autotune(3)
     sched = lat.schedule()
     torch.cuda.synchronize()
-    # the state the timed window starts from: the end-to-end loop below advances this state (the cost
-    # of an MCS depends on how many sites can change, which falls as the run goes on)
-    window_start_words = None if args.no_e2e else lat.get_packed()[0]
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -507,20 +504,29 @@ def main():
 
     # end to end through the public API with host buffers: every step uploads its input lattice
     # from pinned memory (in its bit-packed host form, L*L/8 bytes, for either device layout),
-    # runs one MCS and reads its cooperator count back to the host
+    # runs one MCS and reads its cooperator count back to the host. The inputs are the timed
+    # window's own states (MCS W .. W+K-1, regenerated untimed from the same seed), taken in turn,
+    # so the end-to-end figure covers the same work as `value`
     e2e = None
     if not args.no_e2e:
-        pinned = torch.from_numpy(window_start_words.reshape(-1).view(np.int32)).pin_memory()
         h2d = L * L // 8
-        reps = 50
+        lat.seed(args.seed + rank, 0.5)
+        lat.advance(args.warmup)
+        states, want = [], []
+        for i in range(args.steps):
+            words, step = lat.get_packed()
+            states.append((torch.from_numpy(words.reshape(-1).view(np.int32)).pin_memory(), step))
+            want.append(int(lat.step_mcs(1)[0]))
+        reps = max(50, args.steps)
         # serial: synchronous upload, one MCS, the count read back by the same call
         counts = np.zeros(1, dtype=np.uint64)
-        lat.set_packed_from_pointer(pinned.data_ptr(), 0)   # untimed: first-use buffers
+        lat.set_packed_from_pointer(states[0][0].data_ptr(), states[0][1])   # untimed: first-use buffers
         lat.step_mcs(1, counts)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(reps):
-            lat.set_packed_from_pointer(pinned.data_ptr(), 0)
+        for r_ in range(reps):
+            host, step = states[r_ % args.steps]
+            lat.set_packed_from_pointer(host.data_ptr(), step)
             lat.step_mcs(1, counts)
         serial = L * L * reps / (time.perf_counter() - t0)
         # overlapped: step i+1's input is staged on the context's copy stream while step i runs;
@@ -529,12 +535,13 @@ def main():
         host_counts = torch.zeros(reps, dtype=torch.int64).pin_memory()
         done = [torch.cuda.Event() for _ in range(reps)]
         read = []
-        lat.stage_packed_from_pointer(pinned.data_ptr(), 0)   # untimed: copy stream and buffers
+        lat.stage_packed_from_pointer(states[0][0].data_ptr(), states[0][1])   # untimed: copy stream
         lat.step_mcs(1, dev_counts[0].data_ptr())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(reps):
-            lat.stage_packed_from_pointer(pinned.data_ptr(), 0)
+            host, step = states[i % args.steps]
+            lat.stage_packed_from_pointer(host.data_ptr(), step)
             lat.step_mcs(1, dev_counts[i].data_ptr())
             host_counts[i].copy_(dev_counts[i], non_blocking=True)
             done[i].record(stream)
@@ -544,14 +551,14 @@ def main():
         done[-1].synchronize()
         read.append(int(host_counts[-1]))
         el = time.perf_counter() - t0
-        # every step advanced the same input from the same step counter: one count
-        assert len(set(read)) == 1 and read[0] == int(counts[0]), "end-to-end steps disagree"
+        # every step reproduces the count of its window MCS
+        assert read == [want[i % args.steps] for i in range(reps)], "end-to-end steps disagree"
         e2e = {"value": L * L * reps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8, "steps": reps,
                "path": "pgg_stage_lattice_packed(pinned host, L*L/8 bytes) + pgg_step_mcs(1, device "
                        "count) + count copied to pinned host memory and read each step; the upload "
-                       "of step i+1 overlaps step i; every step advances the lattice the timed window "
-                       "starts from (MCS W)",
+                       "of step i+1 overlaps step i; the inputs are the timed window's states "
+                       "(MCS W .. W+K-1) in turn",
                "serial": {"value": serial, "path": "pgg_set_lattice_packed (synchronous) + "
                                                    "pgg_step_mcs(1, host count)"}}
 
