@@ -400,9 +400,10 @@ def main():
     for _ in range(args.warmup):
         lat.advance(1)
     if args.kernel == "auto" and not args.no_autotune:
-        # untimed, on the state the timed window starts from (update costs depend on how many sites
-        # can change); restores the lattice and step counter
-        tuned = lat.autotune(3)
+        # untimed, on the state the timed window starts from and over as many MCS as the window
+        # (update costs depend on how many sites can change, which falls along the window);
+        # restores the lattice and step counter
+        tuned = lat.autotune(max(3, min(args.steps, 1000)))
     sched = lat.schedule()
     torch.cuda.synchronize()
 

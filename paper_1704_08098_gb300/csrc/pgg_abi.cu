@@ -129,6 +129,10 @@ struct pgg_ctx {
     uint32_t *mailbox_d = nullptr;
     unsigned int *ctr_d = nullptr;
     unsigned int ctr_launches = 0;  // resident launches since ctr_d was last zeroed
+    // the resident kernel's per-MCS count slots: kResidentCountSlots sums, then as many tallies;
+    // zero between launches, except after a launch that stopped on a time-out
+    unsigned long long *count_slots_d = nullptr;
+    bool count_slots_dirty = true;
     int *status_d = nullptr;
     int *status_h = nullptr;                  // pinned: the status word read back with the counts
     unsigned long long *counts_h = nullptr;   // pinned: counts on their way to a host buffer
@@ -348,6 +352,7 @@ void timing_release(pgg_ctx *c) {
 // Report (and clear) a bounded wait that ran out in an earlier resident launch.
 int status_result(pgg_ctx *c, int st) {
     if (st) {
+        c->count_slots_dirty = true;  // a stopped resident launch may have left count slots in use
         PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
         PGG_CUDA(cudaStreamSynchronize(c->stream));
         c->running_valid = false;
@@ -547,7 +552,6 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
     if (rc) return rc;
     const Schedule s = resolve_schedule(c);
     if (s.kernel == PGG_KERNEL_TILED && s.k > 1 && (rc = ensure_alt(c))) return rc;
-    PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, static_cast<size_t>(n_mcs) * sizeof(unsigned long long), c->stream));
     if (s.kernel == PGG_KERNEL_RESIDENT) {
         const int bands = s.tile_x;
         if (bands < 1) return fail(PGG_ERR_STATE, "pgg_step_mcs: the lattice cannot be resident");
@@ -557,7 +561,16 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             cudaError_t e = cudaMalloc(&c->mailbox_d, (mb_words + bands) * sizeof(uint32_t));
             if (e == cudaSuccess) e = cudaMalloc(&c->ctr_d, sizeof(unsigned int) * bands);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->mailbox_d + mb_words, 0, sizeof(uint32_t) * bands, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMalloc(&c->count_slots_d, pgg::kResidentCountSlots * (sizeof(unsigned long long) + sizeof(unsigned int)));
             if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(resident buffers): %s", cudaGetErrorString(e));
+        }
+        // the kernel writes every count of the call itself (no memset of counts_d); its count
+        // slots must be zero, which they are after every launch that ran to its end
+        if (c->count_slots_dirty) {
+            PGG_CUDA(cudaMemsetAsync(c->count_slots_d, 0,
+                                     pgg::kResidentCountSlots * (sizeof(unsigned long long) + sizeof(unsigned int)), c->stream));
+            c->count_slots_dirty = false;
         }
         // the kernel keeps the band bit-packed in shared memory; a uint8 lattice is packed as it is
         // staged and unpacked as it is written back
@@ -575,7 +588,10 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         a.status = c->status_d;
         a.spin_limit = c->spin_limit;
         a.steps_per_exchange = s.tile_y;
+        a.class_copy = pgg::resident_class_copy(c->L, bands, s.tile_y, c->smem_optin);
         a.hint = reinterpret_cast<unsigned int *>(c->mailbox_d + mb_words);
+        a.count_acc = c->count_slots_d;
+        a.count_tick = reinterpret_cast<unsigned int *>(c->count_slots_d + pgg::kResidentCountSlots);
         // the pass over active sites only wins for the group game up to about 10 % of a step's
         // sites adopting (measured at L = 8192); the pairwise game, whose active sites are more
         // numerous and cheaper to update whole words at a time, takes the dense pass above 1.5 %
@@ -599,6 +615,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         PGG_CUDA(cudaGetLastError());
         return coop_per_mcs ? deliver_counts(c, coop_per_mcs, n_mcs) : PGG_OK;
     }
+    PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, static_cast<size_t>(n_mcs) * sizeof(unsigned long long), c->stream));
     if (s.kernel == PGG_KERNEL_DIRECT) {
         if (!c->running_d) {
             cudaError_t e = cudaMalloc(&c->running_d, sizeof(unsigned long long));
@@ -1036,6 +1053,7 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->running_d) cudaFree(c->running_d);
     if (c->mailbox_d) cudaFree(c->mailbox_d);
     if (c->ctr_d) cudaFree(c->ctr_d);
+    if (c->count_slots_d) cudaFree(c->count_slots_d);
     if (c->status_d) cudaFree(c->status_d);
     if (c->status_h) cudaFreeHost(c->status_h);
     timing_release(c);

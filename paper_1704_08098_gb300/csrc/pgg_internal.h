@@ -87,20 +87,28 @@ struct ResidentArgs {
     unsigned int ctr_base;        // a launch publishes ctr_base + completed steps: every value an
                                   // earlier launch left is below it, so ctr needs no reset
     bool reset_ctr;               // zero ctr before the launch (first use, or ctr_base wrapped)
-    unsigned long long *counts;   // n_mcs counts, zeroed by the caller
+    unsigned long long *counts;   // n_mcs counts (nullable), written by the launch: no zeroing needed
+    unsigned long long *count_acc = nullptr;  // kResidentCountSlots sums and
+    unsigned int *count_tick = nullptr;       // kResidentCountSlots band tallies, all zero before the
+                                              // launch; a launch that ends normally leaves them zero
     int *status;                  // | 1 a bounded wait ran out, | 2 the alignment check failed, | 4 an index
                                   // check failed (checked build), | 8 a CTA stopped with a halo load
                                   // possibly in flight (fatal for the device context)
     unsigned int spin_limit;      // polls before a wait gives up
     int steps_per_exchange = 1;   // sublattice steps between halo exchanges: 1, 2 or 4
+    bool class_copy = false;      // keep and scan a column-class copy (resident_class_copy must hold)
     unsigned int *hint = nullptr; // n_bands words kept between launches (pass-choice hint), nullable
     unsigned int dense_per_mille = 100;  // a step takes the dense pass when the previous one flipped
                                          // more than this share (per mille) of its sites
 };
+// Count slots of the resident kernel: MCS m of a launch sums its band counts in slot m mod this.
+constexpr int kResidentCountSlots = 64;
 int resident_bands(int layout, int L, int sms, size_t smem_optin);
 // Largest steps_per_exchange (4, 2 or 1) whose halo rows fit the shared memory.
 int resident_max_steps_per_exchange(int L, int n_bands, size_t smem_optin);
 size_t resident_mailbox_words(int L, int n_bands);
+// Whether the column-class copy fits beside the rows for s steps per exchange.
+bool resident_class_copy(int L, int n_bands, int s, size_t smem_optin);
 cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s);
 
 }  // namespace pgg

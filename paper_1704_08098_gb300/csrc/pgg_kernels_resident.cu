@@ -29,8 +29,8 @@
 // draw (the stream is counter based). Each warp therefore scans words of its sublattice rows
 // (8 sites per 32-column word, the direction draws of 8 words from one Philox call), finds the
 // active sites (s_x != s_y for the drawn neighbour y), and appends them to a ring in shared
-// memory (active words first, then their sites); whenever 64 sites are waiting, the warp updates
-// them, two per lane: the group counts S_x and S_y from the 7 x 7 neighbourhood of x (population
+// memory (active words first, then their sites); whenever 32 sites are waiting, the warp updates
+// them, one per lane: the group counts S_x and S_y from the 7 x 7 neighbourhood of x (population
 // counts of masked bits), the threshold of Eq. (3) from the host-built table, the adoption draw,
 // and an atomic XOR of the site's bit when it adopts. So the costly part runs at full warp width
 // on active sites only. When many sites are active (a random start, the pairwise game), a dense
@@ -71,7 +71,9 @@ struct ResidentParams {
     uint32_t *mailbox;        // [band][parity][top/bottom][H rows][Lw]
     unsigned int *ctr;        // [band] ctr_base + blocks published in this launch
     unsigned int ctr_base;    // above every value an earlier launch left in ctr
-    unsigned long long *counts;  // [n_mcs], zeroed before the launch
+    unsigned long long *counts;  // [n_mcs], written by the launch
+    unsigned long long *count_acc;  // [kResidentCountSlots] band-count sums, zero between launches
+    unsigned int *count_tick;       // [kResidentCountSlots] bands that added to the sum, zero between launches
     int *status;              // | 1 a wait timed out, | 2 misaligned buffers, | 4 an index check failed (checked build),
                               // | 8 a CTA stopped with a halo load possibly still in flight
     unsigned int spin_limit;
@@ -131,8 +133,72 @@ constexpr uint32_t kTwosHi = (1u << (34 - 32)) | (1u << (35 - 32)) | (1u << (36 
 constexpr uint32_t kNearLo = (1u << 19) | (1u << 26) | (1u << 28);
 constexpr uint32_t kNearHi = 1u << (35 - 32);
 
+// --- the column-class copy ----------------------------------------------------------------
+// Beside the bit-packed rows the kernel can keep a second copy of its rows in which a word holds
+// 32 sites of one column class: class-word (c, q) of a row holds columns 128 q + 4 t + c at bit t
+// (t = 0..31), at cls[lr * Lw + c * Lq + q] (Lq = Lw / 4). A sublattice step updates sites of one
+// column class only, so a class-word carries 32 of them, their east and west neighbours sit in the
+// neighbouring classes of the row (class 3 -> 0 one bit along) and the sites above and below in the
+// same class-word of the rows around.
+
+__device__ __forceinline__ uint32_t unshuffle_step(uint32_t x, int sft, uint32_t m) {
+    const uint32_t t = ((x >> sft) ^ x) & m;
+    return x ^ t ^ (t << sft);
+}
+
+// Bit 2 t of x to bit t, bit 2 t + 1 to bit 16 + t (t = 0..15): an outer unshuffle by delta swaps.
+__device__ __forceinline__ uint32_t unzip32(uint32_t x) {
+    x = unshuffle_step(x, 1, 0x22222222u);
+    x = unshuffle_step(x, 2, 0x0C0C0C0Cu);
+    x = unshuffle_step(x, 4, 0x00F000F0u);
+    return unshuffle_step(x, 8, 0x0000FF00u);
+}
+
+// The class bytes of a bit-packed word (column b at bit b): byte 0 = columns 0, 4, .., 28 (class
+// 0), byte 1 = class 2, byte 2 = class 1, byte 3 = class 3 (an outer unshuffle, then one within
+// each half).
+__device__ __forceinline__ uint32_t class_bytes(uint32_t w) {
+    w = unzip32(w);
+    w = unshuffle_step(w, 1, 0x22222222u);
+    w = unshuffle_step(w, 2, 0x0C0C0C0Cu);
+    return unshuffle_step(w, 4, 0x00F000F0u);
+}
+
+// Bits 4 m of f (m = 0..7) to bits m.
+__device__ __forceinline__ uint32_t nibble_bits8(uint32_t f) {
+    f = (f | (f >> 3)) & 0x03030303u;
+    f = (f | (f >> 6)) & 0x000F000Fu;
+    return (f | (f >> 12)) & 0xFFu;
+}
+
+// The class copy of n_rows rows: thread tid of nthr takes groups of 4 bit-packed words (one
+// class-word of each class).
+__device__ __forceinline__ void build_class_rows(const uint32_t *rows, uint32_t *cls, int n_rows, int Lw, int tid, int nthr,
+                                                 int *status) {
+    const int Lq = Lw >> 2;
+    const long long n_words = static_cast<long long>(n_rows) * Lw;
+    for (int g = tid; g < n_rows * Lq; g += nthr) {
+        const int lr = g / Lq, qq = g - lr * Lq;
+        const long long base = static_cast<long long>(lr) * Lw;
+        uint32_t u[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            u[k] = index_ok(base + swz(4 * qq + k), n_words, status) ? class_bytes(rows[base + swz(4 * qq + k)]) : 0u;
+        if (!index_ok(base + 3 * Lq + qq, n_words, status)) continue;
+        uint32_t *cr = cls + base + qq;
+        cr[0] = __byte_perm(__byte_perm(u[0], u[1], 0x0040u), __byte_perm(u[2], u[3], 0x0040u), 0x5410u);
+        cr[2 * Lq] = __byte_perm(__byte_perm(u[0], u[1], 0x0051u), __byte_perm(u[2], u[3], 0x0051u), 0x5410u);
+        cr[Lq] = __byte_perm(__byte_perm(u[0], u[1], 0x0062u), __byte_perm(u[2], u[3], 0x0062u), 0x5410u);
+        cr[3 * Lq] = __byte_perm(__byte_perm(u[0], u[1], 0x0073u), __byte_perm(u[2], u[3], 0x0073u), 0x5410u);
+    }
+}
+
 struct Ctx {
     uint32_t *rows;                       // band + halo rows (local row lr = global row r0 - H + lr)
+    uint32_t *cls;                        // their column-class copy (class-copy kernel only)
+    int Lq;                               // class-words per class and row (Lw / 4)
+    int cprq;                             // 32-class-word chunks per row
+    uint32_t cmagicq;                     // ceil(2^16 / cprq)
     const uint32_t *__restrict__ table;
     int L, Lw, r0, H;
     uint32_t kl, kh_dir, kh_u;            // step index words with the direction / adoption tags
@@ -206,7 +272,7 @@ __device__ __forceinline__ uint32_t site_flip(const Ctx &cx, uint32_t e, int &wo
 // The rings of one warp: active words found by the scan, and the active sites they hold.
 constexpr int kWordRingCap = 64;     // uint2 entries: (activity nibbles, lr << 25 | w << 16 | d16)
 constexpr uint32_t kWordRingMask = kWordRingCap - 1;
-constexpr int kSiteRingCap = 512;    // uint32 entries: lr << 18 | j << 2 | direction (< 64 + 256 held)
+constexpr int kSiteRingCap = 512;    // uint32 entries: lr << 18 | j << 2 | direction (< 32 + 256 held)
 constexpr uint32_t kSiteRingMask = kSiteRingCap - 1;
 
 struct Rings {
@@ -216,24 +282,27 @@ struct Rings {
     uint32_t flips;           // adoptions this thread made in the current step
 };
 
-// Warp-uniform: update the next n (<= 64) active sites, two per lane (sites lane and lane + 32).
-// Both decisions are taken before either bit is flipped, so their loads and Philox rounds
-// interleave; sites of one step never read each other's bits, so the order does not matter.
-template <int GAME>
+// Warp-uniform: update the next n (<= 32) active sites, one per lane. A round is latency bound
+// (the Philox draw and the neighbourhood gather of one site), so rounds of one site per lane end
+// sooner than rounds of two, and a step's last, partial round is the shortest possible; sites of
+// one step never read each other's bits, so the order does not matter.
+// CLS: the kernel keeps the column-class copy, which an adoption flips too.
+template <int GAME, bool CLS>
 __device__ __forceinline__ void drain_sites(const Ctx &cx, Rings &q, uint32_t n, int lane) {
     __syncwarp();
     const uint32_t l = static_cast<uint32_t>(lane);
-    if (l + 32u < n) {
-        int a0, a1;
-        const uint32_t f0 = site_flip<GAME>(cx, q.sites[(q.sh + l) & kSiteRingMask], a0);
-        const uint32_t f1 = site_flip<GAME>(cx, q.sites[(q.sh + l + 32u) & kSiteRingMask], a1);
-        if (f0) atomicXor(&cx.rows[a0], f0);
-        if (f1) atomicXor(&cx.rows[a1], f1);
-        q.flips += (f0 != 0u) + (f1 != 0u);
-    } else if (l < n) {
+    if (l < n) {
         int a0;
-        const uint32_t f0 = site_flip<GAME>(cx, q.sites[(q.sh + l) & kSiteRingMask], a0);
-        if (f0) atomicXor(&cx.rows[a0], f0);
+        const uint32_t e0 = q.sites[(q.sh + l) & kSiteRingMask];
+        const uint32_t f0 = site_flip<GAME>(cx, e0, a0);
+        if (f0) {
+            atomicXor(&cx.rows[a0], f0);
+            if constexpr (CLS) {
+                const uint32_t j = (e0 >> 2) & 0xFFFFu;
+                const long long ci = static_cast<long long>(e0 >> 18) * cx.Lw + (j & 3u) * cx.Lq + (j >> 7);
+                if (index_ok(ci, cx.n_words, cx.status)) atomicXor(&cx.cls[ci], 1u << ((j >> 2) & 31u));
+            }
+        }
         q.flips += f0 != 0u;
     }
     q.sh += n;
@@ -241,8 +310,8 @@ __device__ __forceinline__ void drain_sites(const Ctx &cx, Rings &q, uint32_t n,
 
 // Warp-uniform: turn the next n (<= 32) active words into site entries, one word per lane (the
 // ring positions from a prefix sum of the lanes' site counts, <= 8, by its bits), then update
-// sites while 64 or more are waiting. The site ring holds < 64 entries before and at most
-// 63 + 256 after.
+// sites while 32 or more are waiting. The site ring holds < 32 entries before and at most
+// 31 + 256 after.
 template <int GAME>
 __device__ __forceinline__ void expand_words(const Ctx &cx, Rings &q, uint32_t n, int lane) {
     __syncwarp();
@@ -266,7 +335,7 @@ __device__ __forceinline__ void expand_words(const Ctx &cx, Rings &q, uint32_t n
         ++pos;
         act &= act - 1u;
     }
-    while (q.st - q.sh >= 64u) drain_sites<GAME>(cx, q, 64u, lane);
+    while (q.st - q.sh >= 32u) drain_sites<GAME, false>(cx, q, 32u, lane);
 }
 
 // Activity of the 8 sites of one word (nibble bits): s_x != s_y for the drawn neighbour y; oj: the
@@ -443,7 +512,91 @@ __device__ __forceinline__ bool scan_step(const Ctx &cx, const Range (&rg)[3], i
 template <int GAME>
 __device__ __forceinline__ void flush_rings(const Ctx &cx, Rings &q, int lane) {
     if (q.wt != q.wh) expand_words<GAME>(cx, q, q.wt - q.wh, lane);
-    while (q.st != q.sh) drain_sites<GAME>(cx, q, min(64u, q.st - q.sh), lane);
+    while (q.st != q.sh) drain_sites<GAME, false>(cx, q, min(32u, q.st - q.sh), lane);
+}
+
+// Warp-uniform: append each lane's active sites (act: bit t = site t of its class-word, lo_b / hi_b
+// the two bits of the sites' direction codes, ebase the class-word's entry base) to the site ring,
+// up to 8 per lane and pass (the ring then holds < 32 + 256 entries), updating 32 at a time.
+template <int GAME>
+__device__ __forceinline__ void push_sites(const Ctx &cx, Rings &q, uint32_t act, uint32_t lo_b, uint32_t hi_b,
+                                           uint32_t ebase, int lane) {
+    while (__any_sync(0xffffffffu, act != 0u)) {
+        const uint32_t cnt = min(static_cast<uint32_t>(__popc(act)), 8u);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        uint32_t pos = q.st + incl - cnt;
+        q.st += __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t t = static_cast<uint32_t>(__ffs(act) - 1);
+            act &= act - 1u;
+            q.sites[pos & kSiteRingMask] = ebase + (t << 4) + ((lo_b >> t) & 1u) + (((hi_b >> t) & 1u) << 1);
+            ++pos;
+        }
+        while (q.st - q.sh >= 32u) drain_sites<GAME, true>(cx, q, 32u, lane);
+    }
+}
+
+// The scan of one step on the column-class copy: the class-words of the step's column class in its
+// sublattice rows, one per lane (chunks of 32 class-words, ceil(Lq / 32) per row; chunk K of the
+// ranges' concatenation to warp K mod 16). A lane draws the Philox call that holds its class-word's
+// direction codes (the codes of bit-packed words 4 q .. 4 q + 3: components x, y of call q / 2 for
+// an even q, z, w for an odd one), splits them into each site's first and second bit, selects each
+// site's drawn neighbour among the east, west, south and north class-words, and pushes the sites
+// whose neighbour holds the other strategy. The halo wait as in scan_step. Warp-uniform.
+template <int GAME, class Wait>
+__device__ __forceinline__ bool scan_step_cls(const Ctx &cx, const Range (&rg)[3], int wait_at, Wait wait, Rings &q,
+                                              int warp, int lane) {
+    const int Lq = cx.Lq, cpr = cx.cprq, oj = cx.oj;
+    const int n0 = rg[0].n * cpr, n1 = rg[1].n * cpr, total = n0 + n1 + rg[2].n * cpr;
+    bool waited = wait_at < 0;
+    for (int K = warp; K < total; K += kComputeWarps) {
+        int r = 0, kk = K;
+        if (kk >= n0) {
+            kk -= n0;
+            r = 1;
+            if (kk >= n1) {
+                kk -= n1;
+                r = 2;
+            }
+        }
+        const int qr = static_cast<int>((static_cast<uint32_t>(kk) * cx.cmagicq) >> 16);
+        const int cc = kk - qr * cpr;
+        const int lr = (r == 0 ? rg[0].first : r == 1 ? rg[1].first : rg[2].first) + 4 * qr;
+        if (!waited && r >= wait_at) {
+            if (!wait()) return false;
+            waited = true;
+        }
+        const int qw = 32 * cc + lane;
+        const bool valid = qw < Lq;
+        const int qq = valid ? qw : 0;
+        int i = cx.r0 - cx.H + lr;
+        if (i < 0) i += cx.L;
+        else if (i >= cx.L) i -= cx.L;
+        const uint4 d = philox_rk(
+            make_uint4(static_cast<uint32_t>(qq >> 1), static_cast<uint32_t>(i >> 2), cx.kl, cx.kh_dir), *cx.rk);
+        const uint32_t ua = unzip32((qq & 1) ? d.z : d.x), ub = unzip32((qq & 1) ? d.w : d.y);
+        const uint32_t lo_b = __byte_perm(ua, ub, 0x5410u), hi_b = __byte_perm(ua, ub, 0x7632u);
+        const long long rb = static_cast<long long>(lr) * cx.Lw;
+        const uint32_t *row = cx.cls + rb;
+#define PGG_LDC(OFF) (index_ok(rb + (OFF), cx.n_words, cx.status) ? row[(OFF)] : 0u)
+        const uint32_t sx = PGG_LDC(oj * Lq + qq);
+        const uint32_t yn = PGG_LDC(oj * Lq + qq - cx.Lw), ys = PGG_LDC(oj * Lq + qq + cx.Lw);
+        const uint32_t ye = oj < 3 ? PGG_LDC((oj + 1) * Lq + qq)
+                                   : __funnelshift_r(PGG_LDC(qq), PGG_LDC(qq + 1 == Lq ? 0 : qq + 1), 1);
+        const uint32_t yw = oj > 0 ? PGG_LDC((oj - 1) * Lq + qq)
+                                   : __funnelshift_l(PGG_LDC(3 * Lq + (qq == 0 ? Lq - 1 : qq - 1)), PGG_LDC(3 * Lq + qq), 1);
+#undef PGG_LDC
+        const uint32_t act = valid ? sx ^ mux(hi_b, mux(lo_b, ye, yw), mux(lo_b, ys, yn)) : 0u;
+        push_sites<GAME>(cx, q, act, lo_b, hi_b,
+                         static_cast<uint32_t>(lr) << 18 | static_cast<uint32_t>(128 * qq + oj) << 2, lane);
+    }
+    if (!waited && !wait()) return false;
+    return true;
 }
 
 // The dense pass: every word of the rows, all 8 sites at once by the shared per-word core
@@ -454,7 +607,7 @@ __device__ __forceinline__ void flush_rings(const Ctx &cx, Rings &q, int lane) {
 //
 // Task t goes to thread (first + t) mod T, so that a range that follows another starts at the
 // threads the previous one left one task short. Returns the number of tasks.
-template <int OJ, int GAME>
+template <int OJ, int GAME, bool CLS>
 __device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int tid, int first, uint32_t &flips) {
     if (rg.n <= 0) return 0;
     const int words = rg.n * cx.Lw;
@@ -502,8 +655,14 @@ __device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int ti
             const uint32_t f = game_flips<OJ, GAME>(wl, wc, wr, u, *cx.rk, cx.table, sx);
             // one thread owns the word in this pass: a plain store (the bits other threads read
             // from it are never among the flipped ones)
-            if (f && index_ok(static_cast<long long>(lr) * cx.Lw + swz(w), cx.n_words, cx.status))
+            if (f && index_ok(static_cast<long long>(lr) * cx.Lw + swz(w), cx.n_words, cx.status)) {
                 cx.rows[lr * cx.Lw + swz(w)] = wc[3] ^ (f << OJ);
+                if constexpr (CLS) {
+                    // four words share a class-word, each perhaps in another thread's task
+                    const long long ci = static_cast<long long>(lr) * cx.Lw + OJ * cx.Lq + (w >> 2);
+                    if (index_ok(ci, cx.n_words, cx.status)) atomicXor(&cx.cls[ci], nibble_bits8(f) << (8 * (w & 3)));
+                }
+            }
             flips += __popc(f);
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
@@ -516,30 +675,30 @@ __device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int ti
 }
 
 // One step of the dense pass (the rows and the halo wait as in step_rows).
-template <int OJ, int GAME, class Wait>
+template <int OJ, int GAME, bool CLS, class Wait>
 __device__ __forceinline__ bool step_dense(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
                                            int tid, uint32_t &flips) {
     constexpr int R = kReadRadius<GAME>;
     const int in_lo = cx.H + R, in_hi = cx.H + nb - R;
     if (!split) {
-        dense_rows<OJ, GAME>(cx, srows_in(m4, lo, hi), tid, 0, flips);
+        dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, lo, hi), tid, 0, flips);
         return true;
     }
     int next = 0;
-    if (in_hi > in_lo) next = dense_rows<OJ, GAME>(cx, srows_in(m4, in_lo, in_hi), tid, 0, flips);
+    if (in_hi > in_lo) next = dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, in_lo, in_hi), tid, 0, flips);
     if (!wait()) return false;
     if (in_hi > in_lo) {
-        next += dense_rows<OJ, GAME>(cx, srows_in(m4, lo, in_lo), tid, next, flips);
-        dense_rows<OJ, GAME>(cx, srows_in(m4, in_hi, hi), tid, next, flips);
+        next += dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, lo, in_lo), tid, next, flips);
+        dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, in_hi, hi), tid, next, flips);
     } else {
-        dense_rows<OJ, GAME>(cx, srows_in(m4, lo, hi), tid, 0, flips);
+        dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, lo, hi), tid, 0, flips);
     }
     return true;
 }
 
 // One step: with `split`, first the rows whose reads stay inside the band, then -- once the
 // halo has landed -- the rest; then every remaining active site.
-template <int GAME, class Wait>
+template <int GAME, bool CLS, class Wait>
 __device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
                                           Rings &q, int warp, int lane) {
     constexpr int R = kReadRadius<GAME>;
@@ -558,8 +717,13 @@ __device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi,
         rg[2] = srows_in(m4, in_hi, hi);
         wait_at = 1;
     }
-    if (!scan_step<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
-    flush_rings<GAME>(cx, q, lane);
+    if constexpr (CLS) {
+        if (!scan_step_cls<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
+        while (q.st != q.sh) drain_sites<GAME, true>(cx, q, min(32u, q.st - q.sh), lane);
+    } else {
+        if (!scan_step<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
+        flush_rings<GAME>(cx, q, lane);
+    }
     return true;
 }
 
@@ -625,7 +789,8 @@ __device__ __forceinline__ void compute_barrier() { asm volatile("bar.sync 1, %0
 // suspend the thread for a short time; a bulk copy from L2 lands within microseconds).
 constexpr unsigned int kMbarTries = 1u << 26;
 
-template <int GAME>
+// CLS: keep the column-class copy of the rows and scan it (shared memory for both copies).
+template <int GAME, bool CLS>
 __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_constant__ ResidentParams p) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int R = kReadRadius<GAME>;
@@ -634,9 +799,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const int r0 = band_start(b, L, nbnd), nb = band_start(b + 1, L, nbnd) - r0;
     const int nb_max = (L + nbnd - 1) / nbnd;
     uint32_t *s_table = smem;
-    uint32_t *s_rows = smem + kTableEntries;                                   // (nb_max + 2H) rows
-    uint32_t *s_stage = s_rows + static_cast<size_t>(nb_max + 2 * H) * Lw;    // 2H rows when s > 1
-    uint2 *s_wring = reinterpret_cast<uint2 *>(s_stage + (S > 1 ? static_cast<size_t>(2 * H) * Lw : 0));
+    const size_t rows_words = static_cast<size_t>(nb_max + 2 * H) * Lw;
+    uint32_t *s_rows = smem + kTableEntries;                 // (nb_max + 2H) rows
+    uint32_t *s_cls = s_rows + rows_words;                   // their class copy (CLS)
+    uint32_t *s_stage = s_cls + (CLS ? rows_words : 0);      // 2H rows when s > 1 (and their class copy)
+    uint2 *s_wring = reinterpret_cast<uint2 *>(s_stage + (S > 1 ? static_cast<size_t>(2 * H) * Lw * (CLS ? 2 : 1) : 0));
     uint32_t *s_sring = reinterpret_cast<uint32_t *>(s_wring + kComputeWarps * kWordRingCap);
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ volatile int s_abort;
@@ -646,10 +813,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const bool comm = tid >= kComputeThreads;  // the last warp exchanges halos, the others compute
     const int up = (b + nbnd - 1) % nbnd, down = (b + 1) % nbnd;
     const size_t edge = static_cast<size_t>(H) * Lw;                  // words of H rows
+    const size_t slot = CLS ? 2 * edge : edge;                        // a mailbox side: rows (+ class copy)
     const uint32_t edge_bytes = static_cast<uint32_t>(edge * sizeof(uint32_t));
     const PhiloxKeys &rk = p.rk;  // read from the parameter space: constant operands
     // bulk copies need 16-byte aligned rows (the same answer in every CTA: all stop together)
-    if ((smem_u32(s_rows) & 15u) != 0u || (smem_u32(s_stage) & 15u) != 0u ||
+    if ((smem_u32(s_rows) & 15u) != 0u || (smem_u32(s_cls) & 15u) != 0u || (smem_u32(s_stage) & 15u) != 0u ||
         (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.lat8) & 15u) != 0u) {
         if (tid == 0) atomicOr(p.status, 2);
         return;
@@ -697,9 +865,18 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     copy_async_wait_all();
     fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
     __syncthreads();
+    if constexpr (CLS) {
+        build_class_rows(s_rows, s_cls, n_local, Lw, tid, kResThreads, p.status);
+        fence_async_shared();  // and so are the class copy's
+        __syncthreads();
+    }
 
     Ctx cx;
     cx.rows = s_rows;
+    cx.cls = s_cls;
+    cx.Lq = Lw >> 2;
+    cx.cprq = (cx.Lq + 31) >> 5;
+    cx.cmagicq = (65536u + static_cast<uint32_t>(cx.cprq) - 1u) / static_cast<uint32_t>(cx.cprq);
     cx.table = s_table;
     cx.L = L;
     cx.Lw = Lw;
@@ -741,12 +918,16 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                         s_abort = 1;
                     } else {
                         const int par = (blk - 1) & 1;
-                        const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * edge;
-                        const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * edge;
+                        const uint32_t *from_up = p.mailbox + ((static_cast<size_t>(up) * 2 + par) * 2 + 1) * slot;
+                        const uint32_t *from_down = p.mailbox + ((static_cast<size_t>(down) * 2 + par) * 2 + 0) * slot;
                         fence_async_global();  // the acquired rows, for the async proxy's reads
-                        mbar_expect_tx(&s_mbar, 2 * edge_bytes);
+                        mbar_expect_tx(&s_mbar, (CLS ? 4 : 2) * edge_bytes);
                         bulk_load(s_rows, from_up, edge_bytes, &s_mbar);
                         bulk_load(s_rows + static_cast<size_t>(nb + H) * Lw, from_down, edge_bytes, &s_mbar);
+                        if (CLS) {
+                            bulk_load(s_cls, from_up + edge, edge_bytes, &s_mbar);
+                            bulk_load(s_cls + static_cast<size_t>(nb + H) * Lw, from_down + edge, edge_bytes, &s_mbar);
+                        }
                         load_pending = true;
                     }
                 }
@@ -781,13 +962,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 bool ok = true;
                 if (dense) {
                     switch (o & 3) {
-                        case 0: ok = step_dense<0, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
-                        case 1: ok = step_dense<1, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
-                        case 2: ok = step_dense<2, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
-                        default: ok = step_dense<3, GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        case 0: ok = step_dense<0, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        case 1: ok = step_dense<1, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        case 2: ok = step_dense<2, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        default: ok = step_dense<3, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
                     }
                 } else {
-                    ok = step_rows<GAME>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane);
+                    ok = step_rows<GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane);
                 }
                 // the step's adoptions, for the next step's choice of pass
                 const unsigned int wf = __reduce_add_sync(0xffffffffu, q.flips);
@@ -821,24 +1002,36 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 // read them, so they are snapshotted into the staging rows first.
                 const uint32_t *top = s_rows + static_cast<size_t>(H) * Lw;
                 const uint32_t *bot = s_rows + static_cast<size_t>(nb) * Lw;
+                const uint32_t *ctop = s_cls + static_cast<size_t>(H) * Lw;
+                const uint32_t *cbot = s_cls + static_cast<size_t>(nb) * Lw;
                 if (S > 1) {
                     if (!comm) {
                         for (int x = tid; x < static_cast<int>(edge); x += kComputeThreads) {
                             s_stage[x] = top[x];
                             s_stage[edge + x] = bot[x];
+                            if (CLS) {
+                                s_stage[2 * edge + x] = ctop[x];
+                                s_stage[3 * edge + x] = cbot[x];
+                            }
                         }
                         fence_async_shared();
                     }
                     __syncthreads();
                     top = s_stage;
                     bot = s_stage + edge;
+                    ctop = s_stage + 2 * edge;
+                    cbot = s_stage + 3 * edge;
                 }
                 if (comm) {
                     if (tid == kComputeThreads) {
-                        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 0) * edge;
-                        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 1) * edge;
+                        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 0) * slot;
+                        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 1) * slot;
                         bulk_store(to_top, top, edge_bytes);
                         bulk_store(to_bot, bot, edge_bytes);
+                        if (CLS) {
+                            bulk_store(to_top + edge, ctop, edge_bytes);
+                            bulk_store(to_bot + edge, cbot, edge_bytes);
+                        }
                         bulk_commit_and_wait();
                         fence_async_global();
                         __threadfence();
@@ -857,7 +1050,19 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 if (tid == 0) {
                     unsigned long long tot = 0;
                     for (int w = 0; w < kComputeWarps; ++w) tot += s_warp[w];
-                    atomicAdd(&p.counts[j >> 4], tot);
+                    // MCS m's bands add into slot m mod kResidentCountSlots; the last band to add
+                    // writes the count and clears the slot. A band in block k has waited for its
+                    // neighbours to finish block k - 1, so every band has finished block
+                    // k - n_bands / 2: no band reaches a slot again before it is clear (the launch
+                    // checks the slots cover that lag), and every slot is clear when the launch ends.
+                    const int m = j >> 4, slot = m % kResidentCountSlots;
+                    atomicAdd(&p.count_acc[slot], tot);
+                    __threadfence();
+                    if (atomicAdd(&p.count_tick[slot], 1u) == static_cast<unsigned int>(nbnd) - 1u) {
+                        __threadfence();
+                        p.counts[m] = atomicExch(&p.count_acc[slot], 0ull);
+                        atomicExch(&p.count_tick[slot], 0u);
+                    }
                 }
             }
         }
@@ -885,13 +1090,15 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     }
 }
 
-// Shared memory of a launch: table, band + halo rows, staging rows (s > 1), the warps' rings.
-size_t resident_smem_bytes(int L, int n_bands, int game, int s) {
+// Shared memory of a launch: table, band + halo rows, staging rows (s > 1), both twice with the
+// column-class copy (cls), the warps' rings.
+size_t resident_smem_bytes(int L, int n_bands, int game, int s, bool cls) {
     const int H = kReadRadius<kGroupGame> * s;  // the group game's halo bounds the pairwise game's
     (void)game;
     const size_t Lw = static_cast<size_t>(L / 32);
     const size_t max_rows = static_cast<size_t>((L + n_bands - 1) / n_bands);
-    return sizeof(uint32_t) * (kTableEntries + (max_rows + 2 * H) * Lw + (s > 1 ? 2 * H * Lw : 0)) +
+    const size_t copies = cls ? 2 : 1;
+    return sizeof(uint32_t) * (kTableEntries + copies * ((max_rows + 2 * H) * Lw + (s > 1 ? 2 * H * Lw : 0))) +
            static_cast<size_t>(kComputeWarps) * (kWordRingCap * sizeof(uint2) + kSiteRingCap * sizeof(uint32_t));
 }
 
@@ -906,7 +1113,7 @@ int resident_bands(int layout, int L, int sms, size_t smem_optin) {
     int n = sms;
     while (n > 1 && L / n < kReadRadius<kGroupGame>) --n;
     const int max_rows = (L + n - 1) / n;
-    return resident_smem_bytes(L, n, kGroupGame, 1) <= smem_optin && max_rows + 6 <= kMaxLocalRows && L / 32 <= kMaxRowWords
+    return resident_smem_bytes(L, n, kGroupGame, 1, false) <= smem_optin && max_rows + 6 <= kMaxLocalRows && L / 32 <= kMaxRowWords
                ? n
                : 0;
 }
@@ -915,13 +1122,19 @@ int resident_bands(int layout, int L, int sms, size_t smem_optin) {
 int resident_max_steps_per_exchange(int L, int n_bands, size_t smem_optin) {
     const int max_rows = (L + n_bands - 1) / n_bands;
     for (int s = kMaxStepsPerExchange; s > 1; s >>= 1)
-        if (resident_smem_bytes(L, n_bands, kGroupGame, s) <= smem_optin && L / n_bands >= 3 * s &&
+        if (resident_smem_bytes(L, n_bands, kGroupGame, s, false) <= smem_optin && L / n_bands >= 3 * s &&
             max_rows + 6 * s <= kMaxLocalRows)
             return s;
     return 1;
 }
 
-size_t resident_mailbox_words(int L, int n_bands) { return static_cast<size_t>(n_bands) * 2 * 2 * kMaxHalo * (L / 32); }
+// Whether a launch with s steps per exchange fits the column-class copy beside the rows.
+bool resident_class_copy(int L, int n_bands, int s, size_t smem_optin) {
+    return L % 128 == 0 && resident_smem_bytes(L, n_bands, kGroupGame, s, true) <= smem_optin;
+}
+
+// [band][parity][top, bottom][rows, class copy][H rows][Lw]
+size_t resident_mailbox_words(int L, int n_bands) { return static_cast<size_t>(n_bands) * 2 * 2 * 2 * kMaxHalo * (L / 32); }
 
 cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     if (a.n_bands < 1 || a.L % 256 != 0) return cudaErrorInvalidValue;
@@ -935,6 +1148,9 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.s = a.steps_per_exchange;
     p.H = (a.game == kPairGame ? kReadRadius<kPairGame> : kReadRadius<kGroupGame>) * p.s;
     if (a.L / a.n_bands < p.H) return cudaErrorInvalidValue;  // published rows must be band rows
+    // a band runs at most n_bands / 2 + 1 halo blocks ahead of any other: the count slots must
+    // cover that many MCS (152 bands, 4 steps per block: 20 of 64)
+    if ((a.n_bands / 2 + 2) * p.s > 16 * kResidentCountSlots) return cudaErrorInvalidValue;
     if ((a.L + a.n_bands - 1) / a.n_bands + 2 * p.H > kMaxLocalRows || p.Lw > kMaxRowWords) return cudaErrorInvalidValue;
     p.seed = a.seed;
     p.k0 = a.k0;
@@ -944,14 +1160,21 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.ctr = a.ctr;
     p.ctr_base = a.ctr_base;
     p.counts = a.counts;
+    p.count_acc = a.count_acc;
+    p.count_tick = a.count_tick;
+    if (a.counts && (!a.count_acc || !a.count_tick)) return cudaErrorInvalidValue;
     p.status = a.status;
     p.spin_limit = a.spin_limit;
     p.hint = a.hint;
     p.dense_per_mille = a.dense_per_mille;
     p.rk = philox_round_keys(a.seed);
-    const size_t smem = resident_smem_bytes(a.L, a.n_bands, a.game, p.s);
-    const void *kernel = a.game == kPairGame ? reinterpret_cast<const void *>(k_resident<kPairGame>)
-                                             : reinterpret_cast<const void *>(k_resident<kGroupGame>);
+    const bool cls = a.class_copy;
+    const size_t smem = resident_smem_bytes(a.L, a.n_bands, a.game, p.s, cls);
+    const void *kernel = a.game == kPairGame
+                             ? (cls ? reinterpret_cast<const void *>(k_resident<kPairGame, true>)
+                                    : reinterpret_cast<const void *>(k_resident<kPairGame, false>))
+                             : (cls ? reinterpret_cast<const void *>(k_resident<kGroupGame, true>)
+                                    : reinterpret_cast<const void *>(k_resident<kGroupGame, false>));
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     if (a.reset_ctr) {
