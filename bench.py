@@ -39,18 +39,19 @@ FALLBACK_HBM_GBS = 6800.0
 # ALU pipe / of the FMA-heavy pipe (integer multiply-adds), dram_bytes = dram__bytes_read.sum +
 # dram__bytes_write.sum.
 NCU = {
-    # the resident kernel (active-site and dense passes): means of 9 launches inside the timed window
-    # (MCS 5-7, 13-15, 22-24 of the benchmark command with --no-autotune and the schedule named)
-    "resident:9f87374f47ba399d:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 33660172, "fma_warp_inst": 25270637, "dram_bytes": 8520590},
-    "resident:9f87374f47ba399d:bitpack:8192:16:152:2":
-        {"alu_warp_inst": 34504090, "fma_warp_inst": 26006604, "dram_bytes": 8518059},
-    "resident:9f87374f47ba399d:bitpack:8192:16:152:4":
-        {"alu_warp_inst": 36979227, "fma_warp_inst": 27781282, "dram_bytes": 8526080},
-    "resident-pairwise:9f87374f47ba399d:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 45537800, "fma_warp_inst": 31139998, "dram_bytes": 8533276},
-    "resident:9f87374f47ba399d:u8:8192:16:152:2":
-        {"alu_warp_inst": 37148059, "fma_warp_inst": 27635636, "dram_bytes": 81858446},
+    # the resident kernel (active-site and dense passes; the group game on the column-class copy
+    # where it fits, s <= 2 at L = 8192): means of 9 launches inside the timed window (MCS 5-7,
+    # 13-15, 22-24 of the benchmark command with --no-autotune and the schedule named)
+    "resident:f85d67e927ee7456:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 26716951, "fma_warp_inst": 17848388, "dram_bytes": 8488050},
+    "resident:f85d67e927ee7456:bitpack:8192:16:152:2":
+        {"alu_warp_inst": 27812286, "fma_warp_inst": 19058969, "dram_bytes": 8488505},
+    "resident:f85d67e927ee7456:bitpack:8192:16:152:4":
+        {"alu_warp_inst": 34598750, "fma_warp_inst": 26326267, "dram_bytes": 8512654},
+    "resident-pairwise:f85d67e927ee7456:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 45533701, "fma_warp_inst": 31120689, "dram_bytes": 8536007},
+    "resident:f85d67e927ee7456:u8:8192:16:152:2":
+        {"alu_warp_inst": 30456334, "fma_warp_inst": 20564371, "dram_bytes": 85010574},
     "direct:1385c7b1fc7d18a3:bitpack:8192:1:4:64":
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
 }
