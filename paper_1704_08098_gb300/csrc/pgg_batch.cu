@@ -9,7 +9,10 @@
 // i.e. at most 8 word units per thread per sublattice step), synchronising with a named
 // barrier between sublattice steps. The team loads the lattice once, runs all n_mcs MCS
 // (16 sublattice steps each, the same update rule and random stream as the single-lattice
-// kernels), writes the cooperator count after every MCS, and stores the lattice back.
+// kernels), writes the cooperator count after every MCS, and stores the lattice back. A replica
+// whose count reaches 0 or L^2 is in an absorbing state (all D or all C: every neighbour holds the
+// site's own strategy, so no update can change it): its team writes that count for the remaining
+// MCS and stops, which gives the same lattice, step counter and counts as running them.
 //
 // Shared-memory layout of a replica: row-major words with a per-row rotation,
 // word (row, w) at row * Lw + (w + row) mod Lw, so that the threads of a warp, which work
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_batch(const __grid_constant_
     constexpr int kWarps = CTA_THREADS / 32;
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_job;
-    __shared__ unsigned long long s_count[kWarps];
+    __shared__ unsigned long long s_count[2][kWarps];  // per team, by MCS parity
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         if (threadIdx.x == 0) s_job = static_cast<int>(atomicAdd(p.job_counter, 1u));
@@ -176,7 +179,10 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_batch(const __grid_constant_
                 const int row = x >> lw_log2, w = x & (Lw - 1);
                 s_lat[(row << lw_log2) + ((w + row) & (Lw - 1))] = glat[x];
             }
-            if (tid == 0) s_count[team] = 0;
+            if (tid == 0) {
+                s_count[0][team] = 0;
+                s_count[1][team] = 0;
+            }
             team_sync<kWarps>(team, J.team_warps);
             uint64_t k = step0;
             uint4 ocall = make_uint4(0, 0, 0, 0);
@@ -202,13 +208,18 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) k_batch(const __grid_constant_
                     for (int x = tid; x < words; x += nthr) c += __popc(s_lat[x]);
 #pragma unroll
                     for (int sh = 16; sh > 0; sh >>= 1) c += __shfl_down_sync(0xffffffffu, c, sh);
-                    if (lane == 0) atomicAdd(&s_count[team], c);
+                    if (lane == 0) atomicAdd(&s_count[m & 1][team], c);
                     team_sync<kWarps>(team, J.team_warps);
-                    if (tid == 0) {
-                        p.counts[static_cast<size_t>(rid) * p.n_mcs + m] = static_cast<uint32_t>(s_count[team]);
-                        s_count[team] = 0;
+                    const unsigned long long cnt = s_count[m & 1][team];
+                    // the other slot was last read after the previous MCS, 16 team barriers ago
+                    if (tid == 0) s_count[(m + 1) & 1][team] = 0;
+                    uint32_t *row = p.counts + static_cast<size_t>(rid) * p.n_mcs;
+                    if (tid == 0) row[m] = static_cast<uint32_t>(cnt);
+                    if (cnt == 0 || cnt == static_cast<unsigned long long>(words) * 32) {
+                        // absorbing: the remaining MCS leave the lattice as it is
+                        for (int m2 = m + 1 + tid; m2 < p.n_mcs; m2 += nthr) row[m2] = static_cast<uint32_t>(cnt);
+                        break;
                     }
-                    // the next MCS adds to s_count only after 16 more team barriers
                 }
             }
             // store the lattice back (undo the rotation)
