@@ -125,3 +125,29 @@ def test_batch_rejects_unsupported_sizes(pgg):
         pgg.Batch([64, 96], [4.0, 4.0], 0.5, [1, 2])
     with pytest.raises(pgg.PGGError):
         pgg.Batch([2048], [4.0], 0.5, [1])
+
+
+@pytest.mark.parametrize("p,r", [(0.5, 1.5), (1.0, 4.0), (0.0, 4.0)], ids=["decays", "all-C", "all-D"])
+def test_batch_absorbed_replicas(o, pgg, p, r):
+    """A replica whose count reaches 0 or L^2 stops being updated: its later counts, its lattice
+    and its step counter still equal the oracle's full run, in both halves of a call and across
+    calls (r = 1.5 takes a random start to all-D within a few MCS; all-C and all-D starts are
+    absorbing from the first MCS)."""
+    L = np.array([64, 64, 128, 256], dtype=np.int32)
+    seeds = np.arange(40, 44, dtype=np.uint64)
+    n_mcs = 40
+    with pgg.Batch(L, np.full(4, r), 0.5, seeds) as b:
+        b.seed(p)
+        first = b.step_mcs(n_mcs)
+        second = b.step_mcs(n_mcs)
+        for i in range(4):
+            got, step = b.get(i)
+            lat = o.init(int(L[i]), int(seeds[i]), p)
+            want = o.run(lat, r, 0.5, int(seeds[i]), 0, 2 * n_mcs, threads=THREADS)
+            assert step == 32 * n_mcs
+            assert np.array_equal(np.concatenate([first[i], second[i]]), want.astype(np.uint32)), i
+            assert np.array_equal(got, lat), i
+            if p != 0.5:
+                assert want[0] in (0, int(L[i]) ** 2)
+    if p == 0.5:
+        assert want[n_mcs - 1] == 0  # the decaying replicas are absorbed within the first call
