@@ -107,6 +107,14 @@ __device__ __forceinline__ int band_start(int b, int L, int n) { return static_c
 // (words u c, c = 0..31) then hit 32 different banks.
 __device__ __forceinline__ int swz(int w) { return w ^ ((w >> 5) & 7); }
 
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Named barrier 2: in the last step of a block the compute warps hand the band's edge rows over
+// (arrive, without waiting) once they are updated, and the exchange warp waits for all of them.
+__device__ __forceinline__ void edges_arrive() { asm volatile("bar.arrive 2, %0;" ::"n"(kResThreads) : "memory"); }
+__device__ __forceinline__ void edges_wait() { asm volatile("bar.sync 2, %0;" ::"n"(kResThreads) : "memory"); }
+
 __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -606,15 +614,17 @@ __device__ __forceinline__ bool scan_step_cls(const Ctx &cx, const Range (&rg)[3
 // high cooperator densities).
 //
 // Task t goes to thread (first + t) mod T, so that a range that follows another starts at the
-// threads the previous one left one task short. Returns the number of tasks.
+// threads the previous one left one task short. Returns the number of tasks. tw_set > 0 fixes the
+// words per task (a step split into parts sizes them for the whole step).
 template <int OJ, int GAME, bool CLS>
-__device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int tid, int first, uint32_t &flips) {
+__device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int tid, int first, uint32_t &flips,
+                                          int tw_set = 0) {
     if (rg.n <= 0) return 0;
     const int words = rg.n * cx.Lw;
     // words per task: as many as still give every thread of the round a task; a range that starts
     // mid-round (first > 0) sizes its tasks for the threads that round leaves free
     const int free_thr = kComputeThreads - first % kComputeThreads;
-    const int tw = words >= 4 * free_thr ? 4 : words >= 2 * free_thr ? 2 : 1;
+    const int tw = tw_set > 0 ? tw_set : words >= 4 * free_thr ? 4 : words >= 2 * free_thr ? 2 : 1;
     const int runs = cx.Lw / tw;  // Lw % 8 == 0, so tasks never straddle a direction call
     const int n_tasks = rg.n * runs;
     const uint32_t kh = static_cast<uint32_t>(cx.k >> 32) | kTagDir;
@@ -674,39 +684,78 @@ __device__ __forceinline__ int dense_rows(const Ctx &cx, const Range &rg, int ti
     return n_tasks;
 }
 
-// One step of the dense pass (the rows and the halo wait as in step_rows).
+// One step of the dense pass (the rows, the halo wait and the edge hand-over as in step_rows): up to
+// three parts through one call site, the halo wait before part `wait_before`, the hand-over after
+// part `hand_after`.
 template <int OJ, int GAME, bool CLS, class Wait>
-__device__ __forceinline__ bool step_dense(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
-                                           int tid, uint32_t &flips) {
+__device__ __forceinline__ bool step_dense(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, bool edges,
+                                           Wait wait, int tid, uint32_t &flips) {
     constexpr int R = kReadRadius<GAME>;
-    const int in_lo = cx.H + R, in_hi = cx.H + nb - R;
-    if (!split) {
-        dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, lo, hi), tid, 0, flips);
-        return true;
+    const int H = cx.H, in_lo = H + R, in_hi = H + nb - R;
+    Range part[3] = {{0, 0}, {0, 0}, {0, 0}};
+    int wait_before = -1, hand_after = -1, tw = 0;
+    if (edges) {
+        // the top and bottom H rows (the whole band if it is thinner than 2H), then the rows between
+        // them; words per task for the step as a whole (the edge parts alone would take one each)
+        if (nb >= 2 * H) {
+            part[0] = srows_in(m4, H, 2 * H);
+            part[1] = srows_in(m4, nb, nb + H);
+            part[2] = srows_in(m4, 2 * H, nb);
+            hand_after = 1;
+        } else {
+            part[0] = srows_in(m4, H, H + nb);
+            hand_after = 0;
+        }
+        const int all_words = srows_in(m4, H, H + nb).n * cx.Lw;
+        tw = all_words >= 4 * kComputeThreads ? 4 : all_words >= 2 * kComputeThreads ? 2 : 1;
+    } else if (!split) {
+        part[0] = srows_in(m4, lo, hi);
+    } else if (in_hi > in_lo) {
+        part[0] = srows_in(m4, in_lo, in_hi);
+        part[1] = srows_in(m4, lo, in_lo);
+        part[2] = srows_in(m4, in_hi, hi);
+        wait_before = 1;
+    } else {
+        part[0] = srows_in(m4, lo, hi);
+        wait_before = 0;
     }
     int next = 0;
-    if (in_hi > in_lo) next = dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, in_lo, in_hi), tid, 0, flips);
-    if (!wait()) return false;
-    if (in_hi > in_lo) {
-        next += dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, lo, in_lo), tid, next, flips);
-        dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, in_hi, hi), tid, next, flips);
-    } else {
-        dense_rows<OJ, GAME, CLS>(cx, srows_in(m4, lo, hi), tid, 0, flips);
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        if (k == wait_before && !wait()) return false;
+        next += dense_rows<OJ, GAME, CLS>(cx, part[k], tid, next, flips, tw);
+        if (k == hand_after) {
+            fence_async_shared();  // the edge rows' writes, for the bulk store
+            edges_arrive();
+        }
     }
     return true;
 }
 
 // One step: with `split`, first the rows whose reads stay inside the band, then -- once the
-// halo has landed -- the rest; then every remaining active site.
+// halo has landed -- the rest; then every remaining active site. With `edges` (the last step of a
+// block of s > 1 steps, band rows only, no halo wait), first the band's top and bottom H rows,
+// which the exchange warp publishes as soon as every compute thread has handed them over, then
+// the rows between them.
 template <int GAME, bool CLS, class Wait>
-__device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, Wait wait,
-                                          Rings &q, int warp, int lane) {
+__device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi, int nb, bool split, bool edges,
+                                          Wait wait, Rings &q, int warp, int lane) {
     constexpr int R = kReadRadius<GAME>;
     Range rg[3] = {{0, 0}, {0, 0}, {0, 0}};
     int wait_at = -1;
     // rows [in_lo, in_hi) read band rows only; lo <= H < in_lo and in_hi <= H + nb <= hi
     const int in_lo = cx.H + R, in_hi = cx.H + nb - R;
-    if (!split) {
+    Range interior{0, 0};  // with `edges`: the rows of the second phase
+    if (edges) {
+        const int H = cx.H;
+        if (nb >= 2 * H) {
+            rg[0] = srows_in(m4, H, 2 * H);
+            rg[1] = srows_in(m4, nb, nb + H);
+            interior = srows_in(m4, 2 * H, nb);
+        } else {
+            rg[0] = srows_in(m4, H, H + nb);
+        }
+    } else if (!split) {
         rg[0] = srows_in(m4, lo, hi);
     } else if (in_hi <= in_lo) {  // a band too thin for an interior
         rg[0] = srows_in(m4, lo, hi);
@@ -717,12 +766,21 @@ __device__ __forceinline__ bool step_rows(const Ctx &cx, int m4, int lo, int hi,
         rg[2] = srows_in(m4, in_hi, hi);
         wait_at = 1;
     }
-    if constexpr (CLS) {
-        if (!scan_step_cls<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
-        while (q.st != q.sh) drain_sites<GAME, true>(cx, q, min(32u, q.st - q.sh), lane);
-    } else {
-        if (!scan_step<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
-        flush_rings<GAME>(cx, q, lane);
+#pragma unroll 1
+    for (int phase = 0; phase < (edges ? 2 : 1); ++phase) {
+        if (phase == 1) {  // the edge rows are done: hand them over, then the rows between them
+            fence_async_shared();
+            edges_arrive();
+            rg[0] = interior;
+            rg[1] = Range{0, 0};
+        }
+        if constexpr (CLS) {
+            if (!scan_step_cls<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
+            while (q.st != q.sh) drain_sites<GAME, true>(cx, q, min(32u, q.st - q.sh), lane);
+        } else {
+            if (!scan_step<GAME>(cx, rg, wait_at, wait, q, warp, lane)) return false;
+            flush_rings<GAME>(cx, q, lane);
+        }
     }
     return true;
 }
@@ -779,8 +837,6 @@ __device__ __forceinline__ void copy_async_wait_all() {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // Barrier of the compute warps only (the communication warp does not take part).
 __device__ __forceinline__ void compute_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kComputeThreads) : "memory"); }
@@ -802,8 +858,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const size_t rows_words = static_cast<size_t>(nb_max + 2 * H) * Lw;
     uint32_t *s_rows = smem + kTableEntries;                 // (nb_max + 2H) rows
     uint32_t *s_cls = s_rows + rows_words;                   // their class copy (CLS)
-    uint32_t *s_stage = s_cls + (CLS ? rows_words : 0);      // 2H rows when s > 1 (and their class copy)
-    uint2 *s_wring = reinterpret_cast<uint2 *>(s_stage + (S > 1 ? static_cast<size_t>(2 * H) * Lw * (CLS ? 2 : 1) : 0));
+    uint2 *s_wring = reinterpret_cast<uint2 *>(s_cls + (CLS ? rows_words : 0));
     uint32_t *s_sring = reinterpret_cast<uint32_t *>(s_wring + kComputeWarps * kWordRingCap);
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ volatile int s_abort;
@@ -817,7 +872,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     const uint32_t edge_bytes = static_cast<uint32_t>(edge * sizeof(uint32_t));
     const PhiloxKeys &rk = p.rk;  // read from the parameter space: constant operands
     // bulk copies need 16-byte aligned rows (the same answer in every CTA: all stop together)
-    if ((smem_u32(s_rows) & 15u) != 0u || (smem_u32(s_cls) & 15u) != 0u || (smem_u32(s_stage) & 15u) != 0u ||
+    if ((smem_u32(s_rows) & 15u) != 0u || (smem_u32(s_cls) & 15u) != 0u ||
         (reinterpret_cast<uintptr_t>(p.mailbox) & 15u) != 0u || (reinterpret_cast<uintptr_t>(p.lat8) & 15u) != 0u) {
         if (tid == 0) atomicOr(p.status, 2);
         return;
@@ -899,11 +954,29 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     uint64_t ocall_idx = ~0ull;
     const int n_blocks = 16 * p.n_mcs / S;
     bool load_pending = false;  // communication lane: a halo load not yet seen complete
+    // publish the band's top and bottom H rows (and their class copy) after block blk for the
+    // neighbours' next block: bulk stores straight from the rows, complete before the counter is
+    // released (and before the issuer reaches the step's barrier, after which they change again)
+    auto publish = [&](int blk) {
+        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 0) * slot;
+        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 1) * slot;
+        bulk_store(to_top, s_rows + static_cast<size_t>(H) * Lw, edge_bytes);
+        bulk_store(to_bot, s_rows + static_cast<size_t>(nb) * Lw, edge_bytes);
+        if (CLS) {
+            bulk_store(to_top + edge, s_cls + static_cast<size_t>(H) * Lw, edge_bytes);
+            bulk_store(to_bot + edge, s_cls + static_cast<size_t>(nb) * Lw, edge_bytes);
+        }
+        bulk_commit_and_wait();
+        fence_async_global();
+        __threadfence();
+        store_release(&p.ctr[b], p.ctr_base + static_cast<unsigned int>(blk + 1));
+    };
     for (int blk = 0; blk < n_blocks; ++blk) {
         for (int jb = 0; jb < S; ++jb) {
             const int j = blk * S + jb;
             const uint64_t k = p.k0 + static_cast<uint64_t>(j);
             const bool fresh_halo = jb == 0 && blk > 0;  // the halo is being refreshed for this step
+            const bool edges = S > 1 && jb == S - 1;      // the edge rows go out mid-step
             if (comm) {
                 // fetch the neighbours' rows after block blk - 1 into the halo, asynchronously
                 if (tid == kComputeThreads && fresh_halo) {
@@ -930,6 +1003,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                         }
                         load_pending = true;
                     }
+                }
+                if (edges) {
+                    // the last step of a block with s > 1: its rows are band rows only and read no
+                    // halo; the compute warps update the top and bottom H rows first and hand them
+                    // over, and they go out while the rows between them are updated
+                    edges_wait();
+                    if (tid == kComputeThreads) publish(blk);
                 }
                 __syncwarp();
             } else {
@@ -962,13 +1042,13 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 bool ok = true;
                 if (dense) {
                     switch (o & 3) {
-                        case 0: ok = step_dense<0, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
-                        case 1: ok = step_dense<1, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
-                        case 2: ok = step_dense<2, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
-                        default: ok = step_dense<3, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, tid, q.flips); break;
+                        case 0: ok = step_dense<0, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, edges, wait, tid, q.flips); break;
+                        case 1: ok = step_dense<1, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, edges, wait, tid, q.flips); break;
+                        case 2: ok = step_dense<2, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, edges, wait, tid, q.flips); break;
+                        default: ok = step_dense<3, GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, edges, wait, tid, q.flips); break;
                     }
                 } else {
-                    ok = step_rows<GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, wait, q, warp, lane);
+                    ok = step_rows<GAME, CLS>(cx, m4, lo, hi, nb, fresh_halo, edges, wait, q, warp, lane);
                 }
                 // the step's adoptions, for the next step's choice of pass
                 const unsigned int wf = __reduce_add_sync(0xffffffffu, q.flips);
@@ -996,49 +1076,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
                 return;
             }
             if (fresh_halo) load_pending = false;
-            if (jb == S - 1) {
-                // publish the band's top and bottom H rows for the neighbours' next block. With
-                // s > 1 the next block's first step may update some of them before the copy has
-                // read them, so they are snapshotted into the staging rows first.
-                const uint32_t *top = s_rows + static_cast<size_t>(H) * Lw;
-                const uint32_t *bot = s_rows + static_cast<size_t>(nb) * Lw;
-                const uint32_t *ctop = s_cls + static_cast<size_t>(H) * Lw;
-                const uint32_t *cbot = s_cls + static_cast<size_t>(nb) * Lw;
-                if (S > 1) {
-                    if (!comm) {
-                        for (int x = tid; x < static_cast<int>(edge); x += kComputeThreads) {
-                            s_stage[x] = top[x];
-                            s_stage[edge + x] = bot[x];
-                            if (CLS) {
-                                s_stage[2 * edge + x] = ctop[x];
-                                s_stage[3 * edge + x] = cbot[x];
-                            }
-                        }
-                        fence_async_shared();
-                    }
-                    __syncthreads();
-                    top = s_stage;
-                    bot = s_stage + edge;
-                    ctop = s_stage + 2 * edge;
-                    cbot = s_stage + 3 * edge;
-                }
-                if (comm) {
-                    if (tid == kComputeThreads) {
-                        uint32_t *to_top = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 0) * slot;
-                        uint32_t *to_bot = p.mailbox + ((static_cast<size_t>(b) * 2 + (blk & 1)) * 2 + 1) * slot;
-                        bulk_store(to_top, top, edge_bytes);
-                        bulk_store(to_bot, bot, edge_bytes);
-                        if (CLS) {
-                            bulk_store(to_top + edge, ctop, edge_bytes);
-                            bulk_store(to_bot + edge, cbot, edge_bytes);
-                        }
-                        bulk_commit_and_wait();
-                        fence_async_global();
-                        __threadfence();
-                        store_release(&p.ctr[b], p.ctr_base + static_cast<unsigned int>(blk + 1));
-                    }
-                    __syncwarp();
-                }
+            if (S == 1) {
+                // one step per block: the rows go out after the step (the next step updates them only
+                // after its halo wait, which follows this copy's completion)
+                if (tid == kComputeThreads) publish(blk);
+                __syncwarp();
             }
             if (!comm && (j & 15) == 15 && p.counts) {
                 unsigned long long c = 0;
@@ -1090,15 +1132,15 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     }
 }
 
-// Shared memory of a launch: table, band + halo rows, staging rows (s > 1), both twice with the
-// column-class copy (cls), the warps' rings.
+// Shared memory of a launch: table, band + halo rows (twice with the column-class copy, cls), the
+// warps' rings.
 size_t resident_smem_bytes(int L, int n_bands, int game, int s, bool cls) {
     const int H = kReadRadius<kGroupGame> * s;  // the group game's halo bounds the pairwise game's
     (void)game;
     const size_t Lw = static_cast<size_t>(L / 32);
     const size_t max_rows = static_cast<size_t>((L + n_bands - 1) / n_bands);
     const size_t copies = cls ? 2 : 1;
-    return sizeof(uint32_t) * (kTableEntries + copies * ((max_rows + 2 * H) * Lw + (s > 1 ? 2 * H * Lw : 0))) +
+    return sizeof(uint32_t) * (kTableEntries + copies * (max_rows + 2 * H) * Lw) +
            static_cast<size_t>(kComputeWarps) * (kWordRingCap * sizeof(uint2) + kSiteRingCap * sizeof(uint32_t));
 }
 
