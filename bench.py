@@ -39,19 +39,19 @@ FALLBACK_HBM_GBS = 6800.0
 # ALU pipe / of the FMA-heavy pipe (integer multiply-adds), dram_bytes = dram__bytes_read.sum +
 # dram__bytes_write.sum.
 NCU = {
-    # the resident kernel (active-site and dense passes; the group game on the column-class copy
-    # where it fits, s <= 2 at L = 8192): means of 9 launches inside the timed window (MCS 5-7,
-    # 13-15, 22-24 of the benchmark command with --no-autotune and the schedule named)
-    "resident:f85d67e927ee7456:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 26716951, "fma_warp_inst": 17848388, "dram_bytes": 8488050},
-    "resident:f85d67e927ee7456:bitpack:8192:16:152:2":
-        {"alu_warp_inst": 27812286, "fma_warp_inst": 19058969, "dram_bytes": 8488505},
-    "resident:f85d67e927ee7456:bitpack:8192:16:152:4":
-        {"alu_warp_inst": 34598750, "fma_warp_inst": 26326267, "dram_bytes": 8512654},
-    "resident-pairwise:f85d67e927ee7456:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 45533701, "fma_warp_inst": 31120689, "dram_bytes": 8536007},
-    "resident:f85d67e927ee7456:u8:8192:16:152:2":
-        {"alu_warp_inst": 30456334, "fma_warp_inst": 20564371, "dram_bytes": 85010574},
+    # the resident kernel (active-site and dense passes; the group game on the column-class copy):
+    # means of 9 launches inside the timed window (MCS 5-7, 13-15, 22-24 of the benchmark command
+    # with --no-autotune and the schedule named)
+    "resident:90663dd398f7efad:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 27048267, "fma_warp_inst": 17557650, "dram_bytes": 8488363},
+    "resident:90663dd398f7efad:bitpack:8192:16:152:2":
+        {"alu_warp_inst": 28627770, "fma_warp_inst": 18671538, "dram_bytes": 8487737},
+    "resident:90663dd398f7efad:bitpack:8192:16:152:4":
+        {"alu_warp_inst": 30861036, "fma_warp_inst": 19974046, "dram_bytes": 8488363},
+    "resident-pairwise:90663dd398f7efad:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 46606566, "fma_warp_inst": 31826118, "dram_bytes": 8472434},
+    "resident:90663dd398f7efad:u8:8192:16:152:2":
+        {"alu_warp_inst": 31271624, "fma_warp_inst": 20176834, "dram_bytes": 85486222},
     "direct:1385c7b1fc7d18a3:bitpack:8192:1:4:64":
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
 }
