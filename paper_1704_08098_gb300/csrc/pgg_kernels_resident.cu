@@ -20,9 +20,17 @@
 //
 // The exchange runs beside the computation: one extra warp per CTA polls the neighbours'
 // counters, fetches their edge rows into the halo with TMA bulk copies (cp.async.bulk,
-// completion on an mbarrier) and, after each block, bulk-stores the band's own edge rows and
-// releases its counter, while the 16 compute warps update the rows that do not read the halo;
-// the compute warps wait on the mbarrier only before the rows that do.
+// completion on an mbarrier) and bulk-stores the band's own edge rows and releases its counter,
+// while the 16 compute warps update the rows that do not read the halo; the compute warps wait on
+// the mbarrier only before the rows that do. With s > 1 the last step of a block (band rows
+// only, no halo wait) updates the top and bottom H rows first and hands them over through a named
+// barrier, so they go out while the rows between them are updated; the exchange warp's copy has
+// read them before the step ends, after which they change again. With s = 1 they go out after
+// the step: the next step touches them only after its own halo wait, which follows the copy.
+//
+// Where shared memory allows (the group game), the CTA also keeps its rows as a column-class copy,
+// 32 sites of one column class j mod 4 per word, and scans that for the active sites of a step;
+// adoptions flip both copies and the exchange carries both (see the class-copy helpers below).
 //
 // Work within a step: most sites of a sublattice step cannot change, because an update with
 // s_x = s_y is a no-op (Eq. (3) only matters when the strategies differ) and needs no adoption
