@@ -9,7 +9,8 @@
 // and backward passes read.
 //
 // Every kernel accumulates in a fixed order (one thread per output, sequential sums), so the
-// results are deterministic. The whole training step is about 20 MFLOP for B = 256, far too
+// results are deterministic; the hidden layers' forward and weight-gradient kernels stage their
+// operands through shared memory for coalesced reads and keep that order. The whole training step is about 20 MFLOP for B = 256, far too
 // small for tensor cores to matter: plain FMA kernels keep it simple and exact to reason about.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -46,6 +47,35 @@ __global__ void k_dense(const float *__restrict__ X, const __nv_bfloat16 *__rest
     for (int i = 0; i < n_in; ++i) acc = fmaf(__bfloat162float(w[i]), x[i], acc);
     A[idx] = acc;
     if (H) H[idx] = fmaxf(acc, 0.0f);
+}
+
+// The same for n_out % 32 == 0 through shared memory: a 256-thread block computes 32 outputs
+// (lane) of 8 rows (warp); W and X pass through shared memory in chunks of 32 inputs, read with
+// consecutive addresses across the lanes (a thread of k_dense walks its own weight row, so a warp's
+// weight loads lie n_in elements apart). Each thread sums its output over the inputs in the same
+// order as k_dense, with the same operands, so the results are the same bit for bit.
+__global__ void __launch_bounds__(256) k_dense_tiled(const float *__restrict__ X, const __nv_bfloat16 *__restrict__ W,
+                                                     const __nv_bfloat16 *__restrict__ bias, float *__restrict__ A,
+                                                     float *__restrict__ H, int B, int n_in, int n_out) {
+    __shared__ float ws[32][33];  // [output][input], padded: lanes read a column without conflicts
+    __shared__ float xs[8][32];   // [row][input]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int o0 = blockIdx.y * 32, o = o0 + lane, b = blockIdx.x * 8 + warp;  // rows in x: up to 2^20 of them
+    float acc = __bfloat162float(bias[o]);
+    for (int i0 = 0; i0 < n_in; i0 += 32) {
+        const int ni = min(32, n_in - i0);
+        for (int rr = warp; rr < 32; rr += 8)
+            ws[rr][lane] = lane < ni ? __bfloat162float(W[static_cast<size_t>(o0 + rr) * n_in + i0 + lane]) : 0.0f;
+        xs[warp][lane] = b < B && lane < ni ? X[static_cast<size_t>(b) * n_in + i0 + lane] : 0.0f;
+        __syncthreads();
+        if (b < B)
+            for (int ii = 0; ii < ni; ++ii) acc = fmaf(ws[lane][ii], xs[warp][ii], acc);
+        __syncthreads();
+    }
+    if (b < B) {
+        A[static_cast<size_t>(b) * n_out + o] = acc;
+        if (H) H[static_cast<size_t>(b) * n_out + o] = fmaxf(acc, 0.0f);
+    }
 }
 
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
@@ -96,20 +126,31 @@ __global__ void k_dense_bwd_data(const float *__restrict__ dA, const __nv_bfloat
     dAprev[idx] = Aprev[idx] > 0.0f ? acc : 0.0f;
 }
 
-// gW[o][i] = sum_b dA[b][o] Xin[b][i]; gb[o] = sum_b dA[b][o] (thread per output, b in order).
-__global__ void k_dense_bwd_weight(const float *__restrict__ dA, const float *__restrict__ Xin,
-                                   float *__restrict__ gW, float *__restrict__ gb, int B, int n_in, int n_out) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_out * (n_in + 1)) return;
-    const int o = idx / (n_in + 1), i = idx - o * (n_in + 1);
+// gW[o][i] = sum_b dA[b][o] Xin[b][i] and gb[o] = sum_b dA[b][o]: a 256-thread block computes 8
+// outputs (warp) by 32 inputs (lane), input n_in standing for the bias (a column of ones:
+// fmaf(d, 1, acc) rounds exactly as acc + d does). dA and Xin pass through shared memory in chunks
+// of 32 rows, read with consecutive addresses; each thread sums its own output over the rows
+// b = 0 .. B-1 in order, one fmaf per row, so the result does not depend on the launch shape.
+__global__ void __launch_bounds__(256) k_dense_bwd_weight_tiled(const float *__restrict__ dA, const float *__restrict__ Xin,
+                                                                float *__restrict__ gW, float *__restrict__ gb, int B,
+                                                                int n_in, int n_out) {
+    __shared__ float das[32][8];   // [row][output]
+    __shared__ float xs[32][32];   // [row][input]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int o0 = blockIdx.y * 8, i = blockIdx.x * 32 + lane, o = o0 + warp;
     float acc = 0.0f;
-    if (i < n_in) {
-        for (int b = 0; b < B; ++b) acc = fmaf(dA[static_cast<size_t>(b) * n_out + o], Xin[static_cast<size_t>(b) * n_in + i], acc);
-        gW[static_cast<size_t>(o) * n_in + i] = acc;
-    } else {
-        for (int b = 0; b < B; ++b) acc += dA[static_cast<size_t>(b) * n_out + o];
-        gb[o] = acc;
+    for (int b0 = 0; b0 < B; b0 += 32) {
+        const int nb = min(32, B - b0);
+        const int bb_l = threadIdx.x >> 3, oo_l = threadIdx.x & 7;  // 32 rows x 8 outputs
+        das[bb_l][oo_l] = bb_l < nb && o0 + oo_l < n_out ? dA[static_cast<size_t>(b0 + bb_l) * n_out + o0 + oo_l] : 0.0f;
+        for (int bb = warp; bb < 32; bb += 8)
+            xs[bb][lane] = bb >= nb || i > n_in ? 0.0f : i == n_in ? 1.0f : Xin[static_cast<size_t>(b0 + bb) * n_in + i];
+        __syncthreads();
+        for (int bb = 0; bb < nb; ++bb) acc = fmaf(das[bb][warp], xs[bb][lane], acc);
+        __syncthreads();
     }
+    if (o < n_out && i < n_in) gW[static_cast<size_t>(o) * n_in + i] = acc;
+    if (o < n_out && i == n_in) gb[o] = acc;
 }
 
 __global__ void k_adam(float *__restrict__ master, const float *__restrict__ g, float *__restrict__ m,
@@ -164,8 +205,10 @@ namespace {
 int forward(pgg_mlp *n, const float *X, int B) {
     const int T = 256;
     const __nv_bfloat16 *q = n->q;
-    k_dense<<<blocks_for(long(B) * kHid, T), T, 0, n->stream>>>(X, q + kOffW1, q + kOffB1, n->a1, n->h1, B, kIn, kHid);
-    k_dense<<<blocks_for(long(B) * kHid, T), T, 0, n->stream>>>(n->h1, q + kOffW2, q + kOffB2, n->a2, n->h2, B, kHid, kHid);
+    static_assert(kHid % 32 == 0, "hidden layers go through k_dense_tiled");
+    const dim3 grid(static_cast<unsigned>((B + 7) / 8), kHid / 32);
+    k_dense_tiled<<<grid, 256, 0, n->stream>>>(X, q + kOffW1, q + kOffB1, n->a1, n->h1, B, kIn, kHid);
+    k_dense_tiled<<<grid, 256, 0, n->stream>>>(n->h1, q + kOffW2, q + kOffB2, n->a2, n->h2, B, kHid, kHid);
     k_dense<<<blocks_for(long(B) * kOut, T), T, 0, n->stream>>>(n->h2, q + kOffW3, q + kOffB3, n->z, nullptr, B, kHid, kOut);
     PGG_MCUDA(cudaGetLastError());
     return PGG_OK;
@@ -177,11 +220,13 @@ int backward(pgg_mlp *n, const float *X, const float *Y, int B) {
     const __nv_bfloat16 *q = n->q;
     float *g = n->grad;
     k_loss<<<1, 256, 0, n->stream>>>(n->z, Y, n->dz, n->loss, B);
-    k_dense_bwd_weight<<<blocks_for(long(kOut) * (kHid + 1), T), T, 0, n->stream>>>(n->dz, n->h2, g + kOffW3, g + kOffB3, B, kHid, kOut);
+    // weight and bias gradients: 8 outputs x 32 inputs (the last one the bias) per block
+    const dim3 gw3((kHid + 1 + 31) / 32, (kOut + 7) / 8), gw2((kHid + 1 + 31) / 32, kHid / 8), gw1((kIn + 1 + 31) / 32, kHid / 8);
+    k_dense_bwd_weight_tiled<<<gw3, 256, 0, n->stream>>>(n->dz, n->h2, g + kOffW3, g + kOffB3, B, kHid, kOut);
     k_dense_bwd_data<<<blocks_for(long(B) * kHid, T), T, 0, n->stream>>>(n->dz, q + kOffW3, n->a2, n->da2, B, kHid, kOut);
-    k_dense_bwd_weight<<<blocks_for(long(kHid) * (kHid + 1), T), T, 0, n->stream>>>(n->da2, n->h1, g + kOffW2, g + kOffB2, B, kHid, kHid);
+    k_dense_bwd_weight_tiled<<<gw2, 256, 0, n->stream>>>(n->da2, n->h1, g + kOffW2, g + kOffB2, B, kHid, kHid);
     k_dense_bwd_data<<<blocks_for(long(B) * kHid, T), T, 0, n->stream>>>(n->da2, q + kOffW2, n->a1, n->da1, B, kHid, kHid);
-    k_dense_bwd_weight<<<blocks_for(long(kHid) * (kIn + 1), T), T, 0, n->stream>>>(n->da1, X, g + kOffW1, g + kOffB1, B, kIn, kHid);
+    k_dense_bwd_weight_tiled<<<gw1, 256, 0, n->stream>>>(n->da1, X, g + kOffW1, g + kOffB1, B, kIn, kHid);
     PGG_MCUDA(cudaGetLastError());
     return PGG_OK;
 }
