@@ -84,6 +84,26 @@ def test_stored_counters_match_the_current_kernel_sources():
         assert v["alu_warp_inst"] > 0 and v["dram_bytes"] > 0, key
 
 
+def test_kernel_code_hash_ignores_comments_only(tmp_path):
+    """The counter key hashes the kernel sources without their // comments; that is sound only if
+    no "//" stands inside a string literal (an even number of quotes before every "//"), and it must
+    change with the code."""
+    import bench
+    csrc = os.path.join(ROOT, "paper_1704_08098_gb300", "csrc")
+    for name in ("pgg_kernels_resident.cu", "pgg_kernels_direct.cu", "pgg_unit.cuh", "pgg_device.cuh"):
+        for line in open(os.path.join(csrc, name)):
+            if "//" in line:
+                assert line.split("//", 1)[0].count('"') % 2 == 0, (name, line)
+    src = "int a = 1;  // one\n// only a comment\n\nint b = 2;\n"
+    path = str(tmp_path / "probe.cu")
+    open(path, "w").write(src)
+    base = bench.kernel_code(path)
+    open(path, "w").write(src.replace("// one", "// another") + "// more\n")
+    assert bench.kernel_code(path) == base
+    open(path, "w").write(src.replace("int b = 2;", "int b = 3;"))
+    assert bench.kernel_code(path) != base
+
+
 def test_binding_fails_loudly_without_the_library(monkeypatch):
     """No fallback: with the CUDA library absent the binding raises instead of computing anything."""
     from paper_1704_08098_gb300 import pgg
