@@ -133,6 +133,10 @@ struct pgg_ctx {
     // zero between launches, except after a launch that stopped on a time-out
     unsigned long long *count_slots_d = nullptr;
     bool count_slots_dirty = true;
+    // the lattice's column-class copy, kept by resident launches that use it (L*L/32 words); valid
+    // while nothing else has written the lattice since (cleared wherever running_valid is)
+    uint32_t *cls_d = nullptr;
+    bool cls_valid = false;
     int *status_d = nullptr;
     int *status_h = nullptr;                  // pinned: the status word read back with the counts
     unsigned long long *counts_h = nullptr;   // pinned: counts on their way to a host buffer
@@ -312,6 +316,7 @@ int apply_stage(pgg_ctx *c) {
     PGG_CUDA(cudaEventRecord(c->stage_free[b], c->stream));
     c->step = c->stage_step;
     c->running_valid = false;
+    c->cls_valid = false;
     return PGG_OK;
 }
 
@@ -356,6 +361,7 @@ int status_result(pgg_ctx *c, int st) {
         PGG_CUDA(cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
         PGG_CUDA(cudaStreamSynchronize(c->stream));
         c->running_valid = false;
+        c->cls_valid = false;
         if (st & 8)
             return fail(PGG_ERR_CUDA, "a resident-kernel CTA stopped after a time-out while a halo copy into its "
                                       "shared memory was still unconfirmed; results on this device are undefined: "
@@ -534,6 +540,7 @@ int pgg_seed(pgg_ctx *c, uint64_t seed, double p) {
     c->seed = seed;
     c->step = 0;
     c->running_valid = false;
+    c->cls_valid = false;
     return PGG_OK;
 }
 
@@ -592,6 +599,15 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         // steps mostly take the dense pass, only pays for keeping it (measured at L = 8192: 0.154
         // against 0.140 ms per MCS), so it runs on the bit-packed rows alone
         a.class_copy = c->game == PGG_GAME_GROUP && pgg::resident_class_copy(c->L, bands, s.tile_y, c->smem_optin);
+        if (a.class_copy && !c->cls_d) {
+            // without room for it the kernel rebuilds the class copy at every launch
+            if (cudaMalloc(&c->cls_d, static_cast<size_t>(c->L) * c->L / 8) != cudaSuccess) {
+                c->cls_d = nullptr;
+                cudaGetLastError();
+            }
+        }
+        a.cls_g = c->cls_d;
+        a.cls_load = c->cls_valid;
         a.hint = reinterpret_cast<unsigned int *>(c->mailbox_d + mb_words);
         a.count_acc = c->count_slots_d;
         a.count_tick = reinterpret_cast<unsigned int *>(c->count_slots_d + pgg::kResidentCountSlots);
@@ -611,19 +627,23 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
             ++c->ctr_launches;
             if (int rc_t = timing_start(c)) return rc_t;
             PGG_CUDA(pgg::launch_resident(a, c->stream));
+            a.cls_load = a.class_copy && a.cls_g;  // the next launch of a long call finds it there
             if (int rc_t = timing_stop(c)) return rc_t;
             c->step += 16ull * static_cast<uint64_t>(a.n_mcs);
         }
         c->running_valid = false;
+        c->cls_valid = a.class_copy && a.cls_g;
         PGG_CUDA(cudaGetLastError());
         return coop_per_mcs ? deliver_counts(c, coop_per_mcs, n_mcs) : PGG_OK;
     }
+    c->cls_valid = false;  // the kernels below write the lattice without its class copy
     PGG_CUDA(cudaMemsetAsync(c->counts_d, 0, static_cast<size_t>(n_mcs) * sizeof(unsigned long long), c->stream));
     if (s.kernel == PGG_KERNEL_DIRECT) {
         if (!c->running_d) {
             cudaError_t e = cudaMalloc(&c->running_d, sizeof(unsigned long long));
             if (e != cudaSuccess) return fail(PGG_ERR_OOM, "cudaMalloc(running count): %s", cudaGetErrorString(e));
             c->running_valid = false;
+            c->cls_valid = false;
         }
         if (!c->running_valid) {
             PGG_CUDA(cudaMemsetAsync(c->running_d, 0, sizeof(unsigned long long), c->stream));
@@ -632,6 +652,7 @@ int pgg_step_mcs(pgg_ctx *c, int64_t n_mcs, uint64_t *coop_per_mcs) {
         }
     } else {
         c->running_valid = false;
+        c->cls_valid = false;
     }
     for (int64_t m = 0; m < n_mcs; ++m) {
         if (s.kernel == PGG_KERNEL_DIRECT) {
@@ -738,6 +759,7 @@ int pgg_set_lattice(pgg_ctx *c, const uint8_t *host_in, uint64_t step) {
     PGG_CUDA(cudaStreamSynchronize(c->stream));
     c->step = step;
     c->running_valid = false;
+    c->cls_valid = false;
     return PGG_OK;
 }
 
@@ -782,6 +804,7 @@ int pgg_set_lattice_packed(pgg_ctx *c, const uint32_t *host_words_in, uint64_t s
     PGG_CUDA(cudaStreamSynchronize(c->stream));
     c->step = step;
     c->running_valid = false;
+    c->cls_valid = false;
     return PGG_OK;
 }
 
@@ -945,6 +968,7 @@ int pgg_lattice_device_ptr(pgg_ctx *c, void **dev_ptr, uint64_t *bytes) {
     PGG_CUDA(cudaSetDevice(c->device));
     if (int rc_stage = apply_stage(c)) return rc_stage;
     if (dev_ptr) *dev_ptr = c->lat;
+    c->cls_valid = false;  // the caller may write the lattice through the pointer
     if (bytes) *bytes = c->lat_bytes;
     return PGG_OK;
 }
@@ -1004,6 +1028,7 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
             }
             c->step = step0;
             c->running_valid = false;
+            c->cls_valid = false;
             if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) { rc = fail(PGG_ERR_CUDA, "pgg_autotune: %s", cudaGetErrorString(e)); break; }
             rc = pgg_step_mcs(c, n_mcs, nullptr);
             if (rc) break;
@@ -1026,6 +1051,7 @@ int pgg_autotune(pgg_ctx *c, int n_mcs, int *kernel, int *steps_per_launch, int 
     if (e1) cudaEventDestroy(e1);
     c->step = step0;
     c->running_valid = false;
+    c->cls_valid = false;
     c->kernel = kern0;
     c->k_fuse = k0;
     c->tile_x = tx0;
@@ -1057,6 +1083,7 @@ void pgg_destroy(pgg_ctx *c) {
     if (c->mailbox_d) cudaFree(c->mailbox_d);
     if (c->ctr_d) cudaFree(c->ctr_d);
     if (c->count_slots_d) cudaFree(c->count_slots_d);
+    if (c->cls_d) cudaFree(c->cls_d);
     if (c->status_d) cudaFree(c->status_d);
     if (c->status_h) cudaFreeHost(c->status_h);
     timing_release(c);

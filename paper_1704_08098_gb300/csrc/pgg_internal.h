@@ -97,6 +97,8 @@ struct ResidentArgs {
     unsigned int spin_limit;      // polls before a wait gives up
     int steps_per_exchange = 1;   // sublattice steps between halo exchanges: 1, 2 or 4
     bool class_copy = false;      // keep and scan a column-class copy (resident_class_copy must hold)
+    uint32_t *cls_g = nullptr;    // L*L/32 words for the class copy between launches (nullable: rebuilt each launch)
+    bool cls_load = false;        // cls_g holds the class copy of this lattice: stage it instead of building it
     unsigned int *hint = nullptr; // n_bands words kept between launches (pass-choice hint), nullable
     unsigned int dense_per_mille = 100;  // a step takes the dense pass when the previous one flipped
                                          // more than this share (per mille) of its sites

@@ -87,6 +87,9 @@ struct ResidentParams {
     unsigned int spin_limit;
     unsigned int *hint;       // [band] adoptions of the last step of the previous launch (nullable)
     unsigned int dense_per_mille;  // dense pass above this share (per mille) of a step's sites flipped
+    uint32_t *cls_g;          // the lattice's column-class copy in global memory (CLS, nullable): written
+                              // back with the band, and
+    int cls_load;             // staged from there when it holds this lattice (else built from the rows)
     PhiloxKeys rk;
 };
 
@@ -840,6 +843,10 @@ __device__ __forceinline__ void bulk_commit_and_wait() {
 __device__ __forceinline__ void copy_async4(uint32_t *dst, const uint32_t *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// 16-byte global -> shared copy (both 16-byte aligned) in the thread's cp.async group
+__device__ __forceinline__ void copy_async16(uint32_t *dst, const uint32_t *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void copy_async_wait_all() {
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -925,13 +932,29 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
             }
         }
     }
+    // the class copy: staged from the lattice's copy in global memory when it holds this lattice
+    // (16-byte copies, its rows are not swizzled), else built from the rows once they have landed
+    const int q16 = Lw >> 2;  // 16-byte chunks of a row
+    if (CLS && p.cls_load && p.cls_g && tid / q16 < kResThreads / q16) {
+        const int cc = tid % q16, rows_per_pass16 = kResThreads / q16;
+        int g = wrap_small(r0 - H + tid / q16, L);
+        for (int lr = tid / q16; lr < n_local; lr += rows_per_pass16) {
+            if (index_ok(static_cast<long long>(lr) * Lw + 4 * cc + 3, static_cast<long long>(n_local) * Lw, p.status) &&
+                index_ok(static_cast<long long>(g) * Lw + 4 * cc + 3, static_cast<long long>(L) * Lw, p.status))
+                copy_async16(&s_cls[lr * Lw + 4 * cc], &p.cls_g[static_cast<size_t>(g) * Lw + 4 * cc]);
+            g += rows_per_pass16;
+            if (g >= L) g -= L;
+        }
+    }
     copy_async_wait_all();
     fence_async_shared();  // the staged halo rows are later overwritten by bulk loads
     __syncthreads();
     if constexpr (CLS) {
-        build_class_rows(s_rows, s_cls, n_local, Lw, tid, kResThreads, p.status);
-        fence_async_shared();  // and so are the class copy's
-        __syncthreads();
+        if (!(p.cls_load && p.cls_g)) {
+            build_class_rows(s_rows, s_cls, n_local, Lw, tid, kResThreads, p.status);
+            fence_async_shared();  // and so are the class copy's
+            __syncthreads();
+        }
     }
 
     Ctx cx;
@@ -1119,6 +1142,15 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident(const __grid_consta
     }
     __syncthreads();  // the last bulk store has completed (its issuer waited) before the band is stored
     if (tid == 0 && p.hint) p.hint[b] = s_flips[(16 * p.n_mcs - 1) % 3];
+    // the band's class copy, for the next launch on this lattice
+    if (CLS && p.cls_g) {
+        for (int x = tid; x < nb * q16; x += kResThreads) {
+            const int lr = x / q16, cc = x - lr * q16;
+            if (index_ok(static_cast<long long>(r0 + lr) * Lw + 4 * cc + 3, static_cast<long long>(L) * Lw, p.status))
+                *reinterpret_cast<uint4 *>(&p.cls_g[static_cast<size_t>(r0 + lr) * Lw + 4 * cc]) =
+                    *reinterpret_cast<const uint4 *>(&s_cls[(lr + H) * Lw + 4 * cc]);
+        }
+    }
     // store the band (the same column-per-thread walk)
     if (row_first < rows_per_pass) {
         if (p.lat8) {
@@ -1217,6 +1249,8 @@ cudaError_t launch_resident(const ResidentArgs &a, cudaStream_t s) {
     p.spin_limit = a.spin_limit;
     p.hint = a.hint;
     p.dense_per_mille = a.dense_per_mille;
+    p.cls_g = a.class_copy ? a.cls_g : nullptr;
+    p.cls_load = a.class_copy && a.cls_g && a.cls_load ? 1 : 0;
     p.rk = philox_round_keys(a.seed);
     const bool cls = a.class_copy;
     const size_t smem = resident_smem_bytes(a.L, a.n_bands, a.game, p.s, cls);
