@@ -42,16 +42,16 @@ NCU = {
     # the resident kernel (active-site and dense passes; the group game on the column-class copy):
     # means of 9 launches inside the timed window (MCS 5-7, 13-15, 22-24 of the benchmark command
     # with --no-autotune and the schedule named)
-    "resident:06b65163dd744c42:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 27048267, "fma_warp_inst": 17557650, "dram_bytes": 8488363},
-    "resident:06b65163dd744c42:bitpack:8192:16:152:2":
-        {"alu_warp_inst": 28627770, "fma_warp_inst": 18671538, "dram_bytes": 8487737},
-    "resident:06b65163dd744c42:bitpack:8192:16:152:4":
-        {"alu_warp_inst": 30861036, "fma_warp_inst": 19974046, "dram_bytes": 8488363},
-    "resident-pairwise:06b65163dd744c42:bitpack:8192:16:152:1":
-        {"alu_warp_inst": 46606566, "fma_warp_inst": 31826118, "dram_bytes": 8472434},
-    "resident:06b65163dd744c42:u8:8192:16:152:2":
-        {"alu_warp_inst": 31271624, "fma_warp_inst": 20176834, "dram_bytes": 85486222},
+    "resident:0dd74940a8619de6:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 24732707, "fma_warp_inst": 16890979, "dram_bytes": 16880356},
+    "resident:0dd74940a8619de6:bitpack:8192:16:152:2":
+        {"alu_warp_inst": 25961540, "fma_warp_inst": 17912088, "dram_bytes": 16879474},
+    "resident:0dd74940a8619de6:bitpack:8192:16:152:4":
+        {"alu_warp_inst": 27730249, "fma_warp_inst": 19026971, "dram_bytes": 16883314},
+    "resident-pairwise:0dd74940a8619de6:bitpack:8192:16:152:1":
+        {"alu_warp_inst": 46606821, "fma_warp_inst": 31826447, "dram_bytes": 8471580},
+    "resident:0dd74940a8619de6:u8:8192:16:152:2":
+        {"alu_warp_inst": 28605390, "fma_warp_inst": 19541023, "dram_bytes": 101647445},
     "direct:c6f01ffbcae43cda:bitpack:8192:1:4:64":
         {"alu_warp_inst": 3675904, "fma_warp_inst": 3167136, "dram_bytes": 8444928},
 }
