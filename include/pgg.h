@@ -148,7 +148,10 @@ int pgg_seed(pgg_ctx *ctx, uint64_t seed, double p);
  * Eq. (4)), the count after each MCS; it may be device memory (written
  * asynchronously) or host memory (the call then synchronises the stream before
  * returning, and also reports a failed bounded wait or index check of this call's
- * kernels). n_mcs >= 0; n_mcs == 0 is a no-op. */
+ * kernels). n_mcs >= 0; n_mcs == 0 is a no-op. The first call on the resident kernel
+ * allocates its exchange mailbox and count slots and, for the group game where the kernel
+ * keeps one, a column-class copy of the lattice (L*L/8 bytes) that later resident calls
+ * reuse while nothing else has written the lattice. */
 int pgg_step_mcs(pgg_ctx *ctx, int64_t n_mcs, uint64_t *coop_per_mcs);
 
 /* Number of cooperators now (numerator of Eq. (4)) into *out (host). Synchronises the
@@ -243,7 +246,9 @@ int pgg_threshold_table(int game, double r, double K, const double payoff[4], ui
  * that hand the lattice to their own kernels on the same stream. The context may move its
  * lattice between two buffers (fused tiled schedules alternate them; an applied staged upload
  * of a bit-packed context takes over the staging buffer), so query the pointer again after any
- * call that steps or replaces the lattice. */
+ * call that steps or replaces the lattice. The caller may write the lattice through the pointer
+ * until the context's next call: after this call the context treats the lattice as replaced
+ * (the column-class copy a resident step keeps of it is rebuilt at the next such step). */
 int pgg_lattice_device_ptr(pgg_ctx *ctx, void **dev_ptr, uint64_t *bytes);
 
 /* Allocation-free variant of pgg_step_mcs, for callers that cannot allocate device memory:
