@@ -30,14 +30,17 @@
 //
 // Where shared memory allows (the group game), the CTA also keeps its rows as a column-class copy,
 // 32 sites of one column class j mod 4 per word, and scans that for the active sites of a step;
-// adoptions flip both copies and the exchange carries both (see the class-copy helpers below).
+// adoptions flip both copies and the exchange carries both (see the class-copy helpers below). The
+// lattice's class copy stays in global memory between launches (cls_g): a launch stages it while it
+// holds the lattice and builds it from the rows otherwise, and writes the band's part back.
 //
 // Work within a step: most sites of a sublattice step cannot change, because an update with
 // s_x = s_y is a no-op (Eq. (3) only matters when the strategies differ) and needs no adoption
 // draw (the stream is counter based). Each warp therefore scans words of its sublattice rows
-// (8 sites per 32-column word, the direction draws of 8 words from one Philox call), finds the
-// active sites (s_x != s_y for the drawn neighbour y), and appends them to a ring in shared
-// memory (active words first, then their sites); whenever 32 sites are waiting, the warp updates
+// (32 sites per class-word of the step's column class; without the class copy 8 sites per
+// 32-column word, the direction draws of 8 words from one Philox call), finds the active sites
+// (s_x != s_y for the drawn neighbour y), and appends them to a ring in shared memory (without
+// the class copy active words first, then their sites); whenever 32 sites are waiting, the warp updates
 // them, one per lane: the group counts S_x and S_y from the 7 x 7 neighbourhood of x (population
 // counts of masked bits), the threshold of Eq. (3) from the host-built table, the adoption draw,
 // and an atomic XOR of the site's bit when it adopts. So the costly part runs at full warp width
@@ -47,10 +50,10 @@
 // the CTA's previous step; both give the same result. Updates of one step touch disjoint sites
 // and read only bits no other update of the step changes, so they run in place in any order.
 //
-// The count after each MCS is the sum of the bands' population counts. The band is staged
-// with 4-byte cp.async copies and written back once per launch; a uint8 lattice is packed as
-// its band is staged (two 16-byte loads per word) and unpacked as it is written back, so it
-// needs no conversion launches.
+// The count after each MCS is the sum of the bands' population counts, gathered in count slots
+// by the last band to report. The band is staged with 4-byte cp.async copies and written back once
+// per launch; a uint8 lattice is packed as its band is staged (two 16-byte loads per word) and
+// unpacked as it is written back, so it needs no conversion launches.
 #include <cuda_runtime.h>
 
 #include "pgg_device.cuh"
