@@ -614,3 +614,39 @@ def test_autotuned_schedule_is_used_by_auto(o, pgg):
             lat.set_schedule(kernel)
             s = lat.schedule()
             assert s["kernel"] == kernel and (kernel != "resident" or s["tile_x"] > 0)
+
+
+class _DeviceBytes:
+    """A raw device buffer as a CUDA array (zero-copy view for torch)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": (n,), "typestr": "|u1", "version": 3}
+
+
+@pytest.mark.parametrize("layout", ["bitpack", "u8"])
+def test_lattice_written_through_device_pointer(o, pgg, layout):
+    """A lattice the caller writes through pgg_lattice_device_ptr between resident steps is the one
+    the next step advances: the column-class copy the resident kernel keeps between calls belongs
+    to the old lattice and must not be reused."""
+    import torch
+    L = 1024
+    with pgg.Lattice(L, 3.9, 0.5, layout=layout) as lat:
+        lat.set_schedule("resident")
+        lat.seed(5, 0.5)
+        lat.step_mcs(2)  # the kernel now keeps the class copy of this lattice
+        new = o.init(L, 9, 0.3)
+        if layout == "bitpack":
+            words = (new.reshape(L, L // 32, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(-1)
+            host = words.astype(np.uint32).view(np.uint8).reshape(-1)
+        else:
+            host = np.ascontiguousarray(new, dtype=np.uint8).reshape(-1)
+        ptr, nbytes = lat.device_ptr()
+        assert nbytes == host.size
+        view = torch.as_tensor(_DeviceBytes(ptr, nbytes), device="cuda")
+        view.copy_(torch.from_numpy(host).cuda())  # on the context's (current) stream
+        got = lat.step_mcs(3)
+        final, step = lat.get()
+    want = o.run(new, 3.9, 0.5, 5, 32, 3, threads=THREADS)
+    assert step == 80
+    assert np.array_equal(got, want)
+    assert np.array_equal(final, new)
