@@ -149,3 +149,27 @@ def test_host_threshold_table_argument_checks(lib):
     assert lib.pgg_threshold_table(pgg.GAME_PAIRWISE, 4.0, 0.5, None, out) == pgg.PGG_ERR_ARG
     assert lib.pgg_threshold_table(7, 4.0, 0.5, None, out) == pgg.PGG_ERR_ARG
     assert lib.pgg_threshold_table(pgg.GAME_GROUP, 4.0, 0.5, None, out) == pgg.PGG_OK
+
+
+def test_stored_bench_line_keeps_the_contract():
+    """The committed bench line (results/) carries the keys of the benchmark contract, and its
+    figures agree with each other: value = L^2 site updates per step / the mean step time,
+    roofline.frac = achieved / peak, the HBM figure = bytes per update x rate / peak."""
+    import json
+    d = json.load(open(os.path.join(ROOT, "results", "bench_L8192_bitpack_default.json")))
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        assert k in d, k
+    L = d["config"]["L"]
+    assert abs(d["value"] - L * L / (d["ms_per_step"] / 1e3)) <= 1e-6 * d["value"]
+    r = d["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in r, k
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) <= 1e-9
+    assert abs(r["hbm_frac"] - r["hbm_bytes_per_update"] * d["value"] / 1e9 / r["hbm_model"]["peak_gbs"]) <= 1e-6
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == L * L // 8 and e["d2h_bytes_per_step"] == 8
+    assert d["gpu_launches"] >= d["steps"]
+    assert not set(d["clocks"]["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
